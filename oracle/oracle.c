@@ -1,0 +1,422 @@
+/*
+ * CPU oracle for speculative First-Fit graph colouring.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this code.  It shares nothing with
+ * the CUDA path (no headers, helpers or tables) and is deliberately plain,
+ * slow and single-threaded so that each function can be checked against the
+ * paper by eye.
+ *
+ * Paper: Rokos, Gorman, Kelly, "A Fast and Scalable Graph Coloring
+ * Algorithm for Multi-core and Many-core Architectures" (arXiv 1505.04086).
+ *
+ *   oracle_ff          Algorithm 1 (sequential greedy / First-Fit), Sec. 2.1
+ *   oracle_rsoc_det    Algorithm 3 (RSOC), Sec. 3, every round reading the
+ *                      colours as they stood at the end of the previous round
+ *   oracle_2p_det      Algorithm 2 (Catalyurek et al.), Sec. 2.2, same
+ *                      snapshot reading; written independently of the above
+ *   oracle_check       validity + the d+1 bound of Sec. 2.1
+ *   oracle_chi         exact chromatic number by exhaustive search (n <= 12)
+ *   oracle_csr_check   input well-formedness (symmetric, sorted, simple)
+ *
+ * Colours are 1-based; 0 means "not coloured" (Sec. 2.1 numbers colours
+ * 1..d+1 and Algorithm 1 forbids only the colours of *coloured* neighbours).
+ *
+ * Tie-break (which endpoint of a conflicting edge is recoloured):
+ *   ORACLE_TIE_LOWER_KEEPS   v is defective iff some neighbour u < v shares
+ *                            its colour (the lower id keeps its colour)
+ *   ORACLE_TIE_HIGHER_KEEPS  v is defective iff some neighbour u > v shares
+ *                            its colour (the test printed in Algorithms 2, 3)
+ *   ORACLE_TIE_NONE          v is defective iff any neighbour shares its
+ *                            colour; this is the symmetric test whose
+ *                            lock-step livelock Section 5 / Fig. 7 describes
+ *
+ * Iterations count executions of the while-loop body, the last one (which
+ * finds no defect) included; RSOC's round 0 is not counted.  Conflicts are
+ * the sum over iterations of the number of vertices found defective.
+ *
+ * Byte model (reported beside the results; the GPU path counts the same
+ * quantity so both can be compared): per vertex inspected in a round,
+ *   4  if the round reads an explicit worklist (not the first pass over V)
+ *   8  for its two row pointers
+ *   4  for its own colour (detection passes only)
+ *   8  per adjacency entry the step must read (column index + colour):
+ *        tentative colouring / recolouring: all deg(v) entries
+ *        clean vertex under detection: its tie-side entries only
+ *   4  per colour written, 4 per worklist push
+ * A tentative pass over a snapshot in which nothing is coloured needs no
+ * reads (every vertex gets colour 1) and is counted as 4 bytes per vertex.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORACLE_TIE_LOWER_KEEPS = 0, ORACLE_TIE_HIGHER_KEEPS = 1, ORACLE_TIE_NONE = 2 };
+enum { ORACLE_OK = 0, ORACLE_ERR_ARG = 1, ORACLE_ERR_OOM = 2, ORACLE_ERR_NO_CONVERGENCE = 3 };
+
+typedef struct {
+    int64_t iterations;
+    int64_t conflicts;
+    int64_t model_bytes;
+    int32_t colors;          /* max colour */
+    int32_t distinct_colors;
+    int32_t *round_sizes;    /* optional, caller-owned: |L| per iteration */
+    int64_t round_sizes_cap;
+} oracle_stats;
+
+/* ------------------------------------------------------------------ */
+/* First-Fit step (Alg. 1 body)                                        */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Smallest colour k >= 1 that no coloured neighbour of v has, with the
+ * neighbours' colours taken from `col`.  `mark` is scratch of at least
+ * maxdeg+2 entries; mark[k] == stamp means "colour k is taken".  Colours
+ * above deg(v)+1 cannot change the answer (Sec. 2.1: one of 1..d+1 is
+ * always free) and are skipped.
+ */
+static int32_t first_fit(int32_t v, const int32_t *row_ptr, const int32_t *col_idx,
+                         const int32_t *col, int64_t *mark, int64_t stamp)
+{
+    int32_t deg = row_ptr[v + 1] - row_ptr[v];
+    for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+        int32_t c = col[col_idx[k]];
+        if (c >= 1 && c <= deg + 1) mark[c] = stamp;
+    }
+    int32_t k = 1;
+    while (mark[k] == stamp) ++k;
+    return k;
+}
+
+static int32_t max_degree(int32_t n, const int32_t *row_ptr)
+{
+    int32_t d = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > d) d = row_ptr[v + 1] - row_ptr[v];
+    return d;
+}
+
+static void colour_counts(int32_t n, const int32_t *c, oracle_stats *st)
+{
+    if (!st) return;
+    int32_t mx = 0;
+    for (int32_t v = 0; v < n; ++v)
+        if (c[v] > mx) mx = c[v];
+    st->colors = mx;
+    char *seen = (char *)calloc((size_t)mx + 1, 1);
+    int32_t d = 0;
+    if (seen) {
+        for (int32_t v = 0; v < n; ++v)
+            if (c[v] > 0 && !seen[c[v]]) { seen[c[v]] = 1; ++d; }
+        free(seen);
+    }
+    st->distinct_colors = d;
+}
+
+/*
+ * Algorithm 1: visit v = 0..n-1 in natural order and give each the
+ * smallest colour not used by its already-coloured neighbours.
+ * Returns the number of colours used (max colour), or -1 on OOM.
+ */
+int32_t oracle_ff(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *c)
+{
+    if (n < 0) return -1;
+    int32_t dmax = max_degree(n, row_ptr);
+    int64_t *mark = (int64_t *)malloc(((size_t)dmax + 2) * sizeof(int64_t));
+    if (!mark) return -1;
+    for (int32_t k = 0; k < dmax + 2; ++k) mark[k] = -1;
+    for (int32_t v = 0; v < n; ++v) c[v] = 0;
+    int32_t used = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        c[v] = first_fit(v, row_ptr, col_idx, c, mark, v);
+        if (c[v] > used) used = c[v];
+    }
+    free(mark);
+    return used;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 3 (RSOC), snapshot replay                                 */
+/* ------------------------------------------------------------------ */
+
+/* Does the tie-break make v the endpoint that must change when its
+ * neighbour u has the same colour? */
+static int loses_to(int32_t v, int32_t u, int tie)
+{
+    if (tie == ORACLE_TIE_LOWER_KEEPS) return u < v;
+    if (tie == ORACLE_TIE_HIGHER_KEEPS) return u > v;
+    return 1;
+}
+
+/*
+ * Algorithm 3 with every read of round i seeing the colours as they stood
+ * at the end of round i-1 (the deterministic, round-synchronous reading):
+ *
+ *   round 0: every vertex takes First-Fit over the (all-uncoloured)
+ *            snapshot;
+ *   U <- V;
+ *   while U is not empty:
+ *       for v in U: if some neighbour u that v loses to has c(u) == c(v),
+ *                   v takes First-Fit over the snapshot (all neighbours'
+ *                   colours forbidden, whether or not they are defective
+ *                   themselves) and joins L;
+ *       U <- L.
+ *
+ * max_iters bounds the loop; hitting it returns ORACLE_ERR_NO_CONVERGENCE
+ * with the colouring as it stands.
+ */
+int oracle_rsoc_det(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int tie,
+                    int64_t max_iters, int32_t *c, oracle_stats *st)
+{
+    if (n < 0 || !c) return ORACLE_ERR_ARG;
+    int32_t dmax = max_degree(n, row_ptr);
+    int32_t *snap = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *U = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *L = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t *mark = (int64_t *)malloc(((size_t)dmax + 2) * sizeof(int64_t));
+    if (!snap || !U || !L || !mark) {
+        free(snap); free(U); free(L); free(mark);
+        return ORACLE_ERR_OOM;
+    }
+    for (int32_t k = 0; k < dmax + 2; ++k) mark[k] = -1;
+    int64_t stamp = 0, bytes = 0, iters = 0, conflicts = 0;
+
+    /* Round 0: tentative First-Fit of every vertex over the snapshot in
+     * which no vertex is coloured yet. */
+    for (int32_t v = 0; v < n; ++v) snap[v] = 0;
+    for (int32_t v = 0; v < n; ++v) c[v] = first_fit(v, row_ptr, col_idx, snap, mark, stamp++);
+    bytes += 4 * (int64_t)n;
+
+    /* U^0 <- V */
+    int64_t nu = n;
+    for (int32_t v = 0; v < n; ++v) U[v] = v;
+    int first_pass = 1;
+    int rc = ORACLE_OK;
+
+    while (nu > 0) {
+        if (iters >= max_iters) { rc = ORACLE_ERR_NO_CONVERGENCE; break; }
+        ++iters;
+        memcpy(snap, c, (size_t)n * sizeof(int32_t));
+        int64_t nl = 0;
+        for (int64_t i = 0; i < nu; ++i) {
+            int32_t v = U[i];
+            int defective = 0;
+            int64_t tie_side = 0;
+            for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                int32_t u = col_idx[k];
+                if (!loses_to(v, u, tie)) continue;
+                ++tie_side;
+                if (snap[u] == snap[v]) defective = 1;
+            }
+            int32_t deg = row_ptr[v + 1] - row_ptr[v];
+            bytes += (first_pass ? 0 : 4) + 8 + 4;
+            if (defective) {
+                c[v] = first_fit(v, row_ptr, col_idx, snap, mark, stamp++);
+                L[nl++] = v;
+                bytes += 8 * (int64_t)deg + 4 + 4;
+            } else {
+                bytes += 8 * tie_side;
+            }
+        }
+        if (st && st->round_sizes && iters - 1 < st->round_sizes_cap)
+            st->round_sizes[iters - 1] = (int32_t)nl;
+        conflicts += nl;
+        int32_t *t = U; U = L; L = t;
+        nu = nl;
+        first_pass = 0;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->conflicts = conflicts;
+        st->model_bytes = bytes;
+        colour_counts(n, c, st);
+    }
+    free(snap); free(U); free(L); free(mark);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2 (two-phase), snapshot replay                            */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Algorithm 2 with the same round-synchronous reading:
+ *
+ *   U <- V
+ *   while U is not empty:
+ *       phase 1: for v in U, new(v) = First-Fit of v over the colours as
+ *                they stood before this phase; then all new colours land;
+ *       phase 2: L = { v in U : some neighbour u that v loses to has
+ *                c(u) == c(v) } over the colours after phase 1;
+ *       U <- L.
+ *
+ * Written without reference to oracle_rsoc_det; the two replays are
+ * expected to agree (the phase-1 recolouring of iteration k+1 equals the
+ * fused recolouring of RSOC iteration k), which the tests check.
+ */
+int oracle_2p_det(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int tie,
+                  int64_t max_iters, int32_t *c, oracle_stats *st)
+{
+    if (n < 0 || !c) return ORACLE_ERR_ARG;
+    int32_t *before = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *work = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *next = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t dmax = max_degree(n, row_ptr);
+    int32_t *taken = (int32_t *)malloc(((size_t)dmax + 2) * sizeof(int32_t));
+    if (!before || !work || !next || !taken) {
+        free(before); free(work); free(next); free(taken);
+        return ORACLE_ERR_OOM;
+    }
+    for (int32_t v = 0; v < n; ++v) c[v] = 0;
+    int64_t w = 0;
+    for (int32_t v = 0; v < n; ++v) work[w++] = v;
+    int64_t iters = 0, conflicts = 0, bytes = 0;
+    int rc = ORACLE_OK;
+    int first = 1;
+    while (w > 0) {
+        if (iters >= max_iters) { rc = ORACLE_ERR_NO_CONVERGENCE; break; }
+        ++iters;
+        /* Phase 1: tentative colouring from the colours before this phase. */
+        memcpy(before, c, (size_t)n * sizeof(int32_t));
+        int any_coloured = 0;
+        for (int32_t v = 0; v < n && !any_coloured; ++v) any_coloured = before[v] != 0;
+        for (int64_t i = 0; i < w; ++i) {
+            int32_t v = work[i];
+            int32_t deg = row_ptr[v + 1] - row_ptr[v];
+            for (int32_t k = 0; k <= deg + 1; ++k) taken[k] = 0;
+            for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                int32_t cu = before[col_idx[k]];
+                if (cu > 0 && cu <= deg + 1) taken[cu] = 1;
+            }
+            int32_t pick = 1;
+            while (taken[pick]) ++pick;
+            c[v] = pick;
+            if (any_coloured)
+                bytes += (first ? 0 : 4) + 8 + 8 * (int64_t)deg + 4;
+            else
+                bytes += 4;
+        }
+        /* Phase 2: conflict detection on the colours after phase 1. */
+        int64_t nl = 0;
+        for (int64_t i = 0; i < w; ++i) {
+            int32_t v = work[i];
+            int bad = 0;
+            int64_t seen = 0;
+            for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                int32_t u = col_idx[k];
+                int counts = tie == ORACLE_TIE_NONE ||
+                             (tie == ORACLE_TIE_LOWER_KEEPS && u < v) ||
+                             (tie == ORACLE_TIE_HIGHER_KEEPS && u > v);
+                if (!counts) continue;
+                ++seen;
+                if (c[u] == c[v]) bad = 1;
+            }
+            bytes += (first ? 0 : 4) + 8 + 4 + 8 * seen;
+            if (bad) { next[nl++] = v; bytes += 4; }
+        }
+        if (st && st->round_sizes && iters - 1 < st->round_sizes_cap)
+            st->round_sizes[iters - 1] = (int32_t)nl;
+        conflicts += nl;
+        memcpy(work, next, (size_t)nl * sizeof(int32_t));
+        w = nl;
+        first = 0;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->conflicts = conflicts;
+        st->model_bytes = bytes;
+        colour_counts(n, c, st);
+    }
+    free(before); free(work); free(next); free(taken);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Checker                                                             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Returns 0 if c is a proper colouring (no entry (v,u) with c[v] == c[u])
+ * and every colour lies in 1..deg(v)+1 (the Sec. 2.1 bound).  Otherwise it
+ * names the first offending vertex v: -(v+1) if c[v] is out of bounds,
+ * v+1 if v shares its colour with a neighbour.  The max colour and the
+ * number of distinct colours go to *colors / *distinct when given.
+ */
+int64_t oracle_check(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *c,
+                     int32_t *colors, int32_t *distinct)
+{
+    int64_t bad = 0;
+    for (int32_t v = 0; v < n && !bad; ++v) {
+        int32_t deg = row_ptr[v + 1] - row_ptr[v];
+        if (c[v] < 1 || c[v] > deg + 1) { bad = -((int64_t)v + 1); break; }
+        for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k)
+            if (c[col_idx[k]] == c[v]) { bad = (int64_t)v + 1; break; }
+    }
+    if (colors || distinct) {
+        oracle_stats st;
+        memset(&st, 0, sizeof st);
+        colour_counts(n, c, &st);
+        if (colors) *colors = st.colors;
+        if (distinct) *distinct = st.distinct_colors;
+    }
+    return bad;
+}
+
+/*
+ * 0 if the CSR is symmetric, rows strictly increasing (sorted, no repeats),
+ * indices in range and no self-loops; otherwise 1 + offending vertex.
+ */
+int64_t oracle_csr_check(int32_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *col_idx)
+{
+    if (n < 0 || row_ptr[0] != 0 || row_ptr[n] != nnz) return 1;
+    for (int32_t v = 0; v < n; ++v) {
+        if (row_ptr[v + 1] < row_ptr[v]) return (int64_t)v + 1;
+        for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int32_t u = col_idx[k];
+            if (u < 0 || u >= n || u == v) return (int64_t)v + 1;
+            if (k > row_ptr[v] && col_idx[k - 1] >= u) return (int64_t)v + 1;
+            /* u's row must contain v */
+            int found = 0;
+            for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j)
+                if (col_idx[j] == v) { found = 1; break; }
+            if (!found) return (int64_t)v + 1;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact chromatic number (small graphs)                               */
+/* ------------------------------------------------------------------ */
+
+static int try_colour(int32_t n, const uint32_t *adj, int32_t v, int32_t k, int32_t *c)
+{
+    if (v == n) return 1;
+    for (int32_t col = 1; col <= k; ++col) {
+        int ok = 1;
+        for (int32_t u = 0; u < v; ++u)
+            if (((adj[v] >> u) & 1u) && c[u] == col) { ok = 0; break; }
+        if (!ok) continue;
+        c[v] = col;
+        if (try_colour(n, adj, v + 1, k, c)) return 1;
+    }
+    c[v] = 0;
+    return 0;
+}
+
+/* Smallest k such that the graph has a proper k-colouring, found by trying
+ * every assignment in order; n <= 12.  Returns -1 for bad input. */
+int32_t oracle_chi(int32_t n, const int32_t *row_ptr, const int32_t *col_idx)
+{
+    if (n < 0 || n > 12) return -1;
+    if (n == 0) return 0;
+    uint32_t adj[12] = {0};
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) adj[v] |= 1u << col_idx[k];
+    int32_t c[12];
+    for (int32_t k = 1; k <= n; ++k) {
+        memset(c, 0, sizeof c);
+        if (try_colour(n, adj, 0, k, c)) return k;
+    }
+    return n;
+}
