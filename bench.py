@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark: speculative First-Fit colouring (RSOC, arXiv 1505.04086 Sec. 3).
+
+Headline workload: the Kuhn-tetrahedralised 128^3 lattice with ids permuted
+(2,097,152 vertices, 14,484,223 edges), coloured by Algorithm 3 (RSOC) in
+asynchronous mode.  One step = one complete colouring of the resident graph
+through the C ABI (gc_color_async + gc_ctx_stats).  Metric: coloured edges
+per second (|E| / wall time of one colouring).
+
+Also reported on the same line: the deterministic mode, the two-phase
+comparison scheme (Algorithm 2), colours vs sequential First-Fit, p50/p99
+latency, the roofline of the colouring kernel against measured HBM copy
+bandwidth, an end-to-end number through host buffers, and the CPU oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank colours its own replica of the workload
+(the colouring of one graph does not shard); value = all ranks' edges /
+max-over-ranks time.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1505_04086_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = "kuhn3d_128"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+METRIC = "colored edges/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline mode only")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gc_kernels.cu", "gc_internal.h"):
+        with open(os.path.join(ROOT, "paper_1505_04086_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, mode_name):
+    """DRAM bytes per launch of the colouring kernel from a committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[f"{workload}/{mode_name}"]
+        if e.get("kernel_sha") != kernel_source_hash():
+            return None
+        return int(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours
+
+MODES = {
+    "rsoc_async": 0 | 2,        # GC_ALG_RSOC | GC_SCHED_ASYNC (headline)
+    "rsoc_det": 0,              # GC_ALG_RSOC | GC_SCHED_DET
+    "twophase_async": 1 | 2,    # GC_ALG_TWO_PHASE | GC_SCHED_ASYNC
+    "twophase_det": 1,
+}
+
+
+def time_mode(ctx, gc, torch, rp, ci, g, mode, steps, warmup, flush, stream):
+    n, nnz = g.n, g.nnz
+    col = torch.empty(n, dtype=torch.int32, device=rp.device)
+    for _ in range(warmup):
+        rc = gc.gc_color_async(ctx.handle, rp, ci, n, nnz, mode, col, None, stream)
+        assert rc == gc.GC_OK, gc.gc_strerror(rc)
+        rc, st = gc.gc_ctx_stats(ctx.handle)
+        assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    kern_ms, mbytes, rounds, confl, colors = [], [], [], [], []
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()  # evict the graph from L2 between steps (512 MB write)
+        evs[i][0].record(stream)
+        rc = gc.gc_color_async(ctx.handle, rp, ci, n, nnz, mode, col, None, stream)
+        evs[i][1].record(stream)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
+        rc, st = gc.gc_ctx_stats(ctx.handle)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
+        kern_ms.append(st["elapsed_ms"])
+        mbytes.append(st["model_bytes"])
+        rounds.append(st["rounds"])
+        confl.append(st["conflicts"])
+        colors.append(st["colors"])
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    return dict(step_ms=step_ms, kern_ms=kern_ms, model_bytes=mbytes, rounds=rounds,
+                conflicts=confl, colors=colors, final=col)
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q))
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_1505_04086_gb300 import gc
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    g = I.workload(args.workload)
+    E = g.num_edges
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gc.Context(local)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- headline: RSOC async, K timed steps ---------------------------------
+    head = "rsoc_async"
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    barrier()
+    t0 = time.perf_counter()
+    res = time_mode(ctx, gc, torch, rp, ci, g, MODES[head], args.steps, args.warmup, flush, stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    total_ms = float(sum(res["step_ms"]))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * args.steps * E / (total_ms / 1e3)
+
+    # roofline of the colouring kernel
+    peak, peak_kind = measured_peak()
+    mb = float(np.mean(res["model_bytes"]))
+    kms = float(np.mean(res["kern_ms"]))
+    achieved = mb / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
+                "traffic": recorded_traffic(args.workload, head),
+                "kernel": "gc::color_kernel<async>", "algorithmic_bytes_per_launch": int(mb),
+                "kernel_ms": round(kms, 5)}
+
+    # validity of the headline mode, checked on the device (untimed)
+    colors = int(np.max(res["colors"]))
+    col_chk = torch.empty(g.n, dtype=torch.int32, device=dev)
+    rc = gc.gc_color_async(ctx.handle, rp, ci, g.n, g.nnz, MODES[head] | gc.GC_CHECKED, col_chk,
+                           None, stream)
+    rc2, _ = gc.gc_ctx_stats(ctx.handle)
+    if rc != gc.GC_OK or rc2 != gc.GC_OK:
+        raise RuntimeError(f"device check of the colouring failed: {gc.gc_strerror(rc2)}")
+
+    extra = {}
+    if not args.no_extra:
+        for name in ("rsoc_det", "twophase_async", "twophase_det"):
+            k = max(3, min(args.steps, 50))
+            r = time_mode(ctx, gc, torch, rp, ci, g, MODES[name], k, 3, flush, stream)
+            tm = float(np.mean(r["step_ms"]))
+            extra[name] = {"value": round(E / (tm / 1e3), 1), "ms_per_step": round(tm, 4),
+                           "p50_ms": round(pct(r["step_ms"], 50), 4), "p99_ms": round(pct(r["step_ms"], 99), 4),
+                           "rounds": int(np.median(r["rounds"])), "conflicts": int(np.median(r["conflicts"])),
+                           "colors": int(np.max(r["colors"])),
+                           "kernel_frac": round(np.mean(r["model_bytes"]) / (np.mean(r["kern_ms"]) / 1e3) / 1e9 / peak, 4),
+                           "steps": k}
+
+    # --- end to end through the C ABI with host buffers ----------------------
+    # Every step copies the graph from pinned host memory, colours it and
+    # copies the colours back (gc_color with host pointers).
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    h_col = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    k = max(3, min(args.steps, 100))
+    for _ in range(3):
+        gc.gc_color(h_rp, h_ci, g.n, g.nnz, MODES[head], h_col)
+    barrier()
+    times = []
+    for _ in range(k):
+        t1 = time.perf_counter()
+        rc, st = gc.gc_color(h_rp, h_ci, g.n, g.nnz, MODES[head], h_col)
+        times.append(time.perf_counter() - t1)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
+    e2e_s = float(sum(times))
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(ws * k * E / e2e_s, 1), "unit": "edges/s",
+           "h2d_bytes_per_step": int(h_rp.numel() * 4 + h_ci.numel() * 4),
+           "d2h_bytes_per_step": int(h_col.numel() * 4),
+           "p50_ms": round(1e3 * float(np.median(times)), 4), "steps": k,
+           "api": "gc_color (host pointers, pinned)"}
+
+    # --- CPU oracle baseline (rank 0, N=1): also gives sequential FF colours --
+    cpu = None
+    ff_colors = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, ff_colors = cpu_baseline(g, budget_s=12.0)
+
+    launches_per_call = 3  # color_kernel, color_stats_kernel, popcount_kernel
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"{args.workload}_perm", "n": g.n, "edges": E, "nnz": g.nnz,
+                   "mode": "rsoc_async", "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas{ws}"},
+        "p50_ms": round(pct(res["step_ms"], 50), 4), "p99_ms": round(pct(res["step_ms"], 99), 4),
+        "colors": colors, "seq_ff_colors": ff_colors,
+        "colors_vs_ff": round(colors / ff_colors, 4) if ff_colors else None,
+        "rounds": int(np.median(res["rounds"])), "conflicts": int(np.median(res["conflicts"])),
+        "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+        "gpu_launches": launches_per_call * args.steps, "clocks": clocks, "modes": extra,
+        "wall_s": round(wall, 3),
+    }
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(g, budget_s=12.0):
+    """The oracle's Algorithm 3 replay (single-threaded C) on the same graph,
+    repeated until ~budget_s of CPU time; also the colour count of the
+    oracle's sequential First-Fit (Algorithm 1), the quality reference."""
+    import oracle
+    ff_colors = int(oracle.ff(g).max())
+    runs, t_all = 0, 0.0
+    while t_all < budget_s or runs == 0:
+        t0 = time.perf_counter()
+        oracle.rsoc_det(g)
+        t_all += time.perf_counter() - t0
+        runs += 1
+        if runs >= 20:
+            break
+    per = t_all / runs
+    return ({"value": round(g.num_edges / per, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+             "sample": f"oracle.rsoc_det (Algorithm 3 snapshot replay, C, 1 thread) on the full "
+                       f"{g.name} graph x {runs} runs, {per:.3f} s each"}, ff_colors)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, ws, rank):
+    """The CPU oracle as it stands, timed on the host cores: each step colours
+    a permuted Kuhn lattice sized so the run ends within a few minutes."""
+    if rank != 0:
+        return
+    import oracle
+    budget = 150.0
+    steps, warm = args.steps, args.warmup
+    N = 128
+    # estimate from a small lattice; time scales with nnz
+    probe = I.kuhn3d(24)
+    t0 = time.perf_counter()
+    oracle.rsoc_det(probe)
+    tp = max(time.perf_counter() - t0, 1e-4)
+    for cand in (128, 96, 80, 64, 48, 40, 32, 24, 16, 12):
+        est = tp * (cand / 24.0) ** 3 * (steps + warm)
+        N = cand
+        if est <= budget:
+            break
+    g = I.kuhn3d(N)
+    for _ in range(warm):
+        oracle.rsoc_det(g)
+    times = []
+    for _ in range(steps):
+        t1 = time.perf_counter()
+        oracle.rsoc_det(g)
+        times.append(time.perf_counter() - t1)
+    total = float(sum(times))
+    value = steps * g.num_edges / total
+    sample = (f"oracle.rsoc_det (Algorithm 3 snapshot replay, C, 1 thread) on kuhn3d_{N} "
+              f"(ids permuted, {g.n} vertices, {g.num_edges} edges), one colouring per step")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "edges/s",
+            "n_gpus": ws, "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * total / steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": f"{WORKLOAD}_perm", "mode": "rsoc (oracle replay)",
+                       "sample_lattice": N},
+            "cpu_baseline": {"value": round(value, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * gc.h - C ABI of libgc, GB300-native speculative First-Fit graph colouring.
+ *
+ * Method: Rokos, Gorman, Kelly, "A Fast and Scalable Graph Coloring
+ * Algorithm for Multi-core and Many-core Architectures", arXiv 1505.04086.
+ *   - Problem (Sec. 2.1, Algorithm 1): given an undirected graph G(V,E),
+ *     assign every vertex the smallest colour not used by its coloured
+ *     neighbours; colours are 1..d+1 for maximum degree d.
+ *   - GC_ALG_RSOC (Sec. 3, Algorithm 3): round 0 colours all of V
+ *     tentatively; every later round inspects the vertices recoloured in the
+ *     round before, recolours at once those still in conflict and collects
+ *     them for the next round (one barrier per round).
+ *   - GC_ALG_TWO_PHASE (Sec. 2.2, Algorithm 2): tentative colouring of the
+ *     worklist, barrier, separate conflict detection, barrier.
+ *
+ * Graph format (all entry points): symmetric CSR, int32 row pointers
+ * (n+1 entries, row_ptr[0] == 0, row_ptr[n] == nnz) and int32 column indices
+ * (nnz entries).  Rows sorted strictly ascending; no self-loops; every entry
+ * (v,u) has its mirror (u,v).  nnz counts directed entries (2|E|).
+ * GC_VALIDATE checks all of this on the device; without it a malformed
+ * graph gives an unspecified (but memory-safe for in-range indices)
+ * colouring.
+ *
+ * Colours: int32, 1-based, in 1..deg(v)+1 on success; 0 is "uncoloured"
+ * and never appears in a successful result.
+ *
+ * Ownership: the caller owns every array it passes; the library never
+ * frees or keeps them past the call (the server copies what it needs).
+ * Errors are returned as negative status codes; nothing throws across the
+ * ABI.  A gc_ctx is not thread-safe; use one per host thread.  The server
+ * entry points are thread-safe.
+ */
+#ifndef GC_H
+#define GC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+    GC_OK = 0,
+    GC_PENDING = 1,              /* server: request not finished yet */
+    GC_ERR_ARG = -1,             /* bad argument (null pointer, size, flag) */
+    GC_ERR_GRAPH = -2,           /* GC_VALIDATE found a malformed CSR */
+    GC_ERR_OOM = -3,             /* device or host allocation failed */
+    GC_ERR_BUDGET = -4,          /* server: request larger than the budget */
+    GC_ERR_NO_CONVERGENCE = -5,  /* round cap reached with conflicts left */
+    GC_ERR_TIMEOUT = -6,         /* a bounded device wait gave up */
+    GC_ERR_CUDA = -7,            /* a CUDA runtime call failed */
+    GC_ERR_OVERFLOW = -8,        /* internal worklist capacity exceeded */
+    GC_ERR_CHECK = -9,           /* GC_CHECKED found an invalid colouring */
+    GC_ERR_NOT_FOUND = -10       /* server: unknown ticket */
+};
+
+/* ---- mode bits ------------------------------------------------------- */
+enum {
+    GC_ALG_RSOC = 0,             /* Algorithm 3 (default) */
+    GC_ALG_TWO_PHASE = 1,        /* Algorithm 2 */
+    GC_SCHED_DET = 0,            /* every read of a round sees the colours of
+                                    the end of the previous round: results are
+                                    deterministic (default) */
+    GC_SCHED_ASYNC = 2,          /* colours are updated in place while other
+                                    threads read them (the paper's form) */
+    GC_TIE_LOWER_KEEPS = 0,      /* of two equal-coloured neighbours the
+                                    higher id is recoloured (default) */
+    GC_TIE_HIGHER_KEEPS = 4,     /* the lower id is recoloured, as the test
+                                    "V_j > V_i" of Algorithms 2 and 3 reads */
+    GC_VALIDATE = 8,             /* check the CSR on the device first */
+    GC_CHECKED = 16,             /* verify the result on the device after */
+    GC_DEBUG_NO_TIEBREAK = 32,   /* symmetric conflict test: both endpoints
+                                    recolour (the Sec. 5 / Fig. 7 livelock);
+                                    only meaningful with a small max_rounds */
+    GC_NO_COLOR_STATS = 64,      /* skip the max/distinct colour reduction */
+    GC_REPAIR_SNAPSHOT = 128     /* with GC_SCHED_ASYNC and GC_ALG_RSOC: round 0
+                                    runs in place, every later round reads the
+                                    colours of the end of the round before
+                                    (fewer colours on dense cores, more rounds) */
+};
+
+/* ---- device error word bits (gc_stats.error_word) ---------------------- */
+enum {
+    GC_EW_TIMEOUT = 1,
+    GC_EW_NO_CONVERGENCE = 2,
+    GC_EW_OVERFLOW = 4,
+    GC_EW_GRAPH = 8,
+    GC_EW_CHECK = 16
+};
+
+typedef struct {
+    const int32_t *row_ptr;      /* n+1 entries */
+    const int32_t *col_idx;      /* nnz entries */
+} gc_csr;
+
+typedef struct {
+    int32_t rounds;              /* while-loop iterations (the last one, which
+                                    finds no conflict, included; RSOC's round 0
+                                    not counted) */
+    int32_t colors;              /* largest colour used (-1 if not computed) */
+    int64_t conflicts;           /* sum over iterations of |L| */
+    int32_t distinct_colors;     /* number of distinct colours (-1 if not computed) */
+    int32_t error_word;          /* GC_EW_* bits raised on the device */
+    int64_t model_bytes;         /* algorithmic bytes the executed rounds must
+                                    move: per inspected vertex 8 for its row
+                                    pointers, 4 for its worklist entry (not in
+                                    a pass over all of V), 4 for its own colour
+                                    (detection passes); 8 per adjacency entry
+                                    read (index + colour): all entries for a
+                                    (re)colouring, the tie side for a clean
+                                    detection; 4 per colour written and per
+                                    worklist push; 4 per vertex for a pass in
+                                    which nothing is coloured yet */
+    float elapsed_ms;            /* device time of the colouring kernel(s) */
+    int32_t *round_sizes;        /* optional caller-owned HOST array; receives
+                                    |L| of each iteration */
+    int32_t round_sizes_cap;     /* its capacity (entries) */
+} gc_stats;
+
+/* Tuning knobs; zero-initialise for defaults. */
+typedef struct {
+    int32_t max_rounds;          /* iteration cap; 0 = n+1 */
+    int32_t t1;                  /* degree <= t1: thread per vertex (<= 62); 0 = 32 */
+    int32_t t2;                  /* t1 < degree <= t2: warp per vertex; above:
+                                    block per vertex (<= 4096); 0 = 2048 */
+    int32_t tile;                /* worklist entries a warp claims at once
+                                    (multiple of 32, <= 4096); 0 = 64 */
+    int32_t blocks_per_sm;       /* resident blocks per SM; 0 = occupancy max */
+    int32_t tail;                /* once a worklist has at most this many
+                                    vertices (and at most 16x as many adjacency
+                                    entries) a single block finishes the
+                                    colouring; 0 = 2048, -1 = never */
+    int32_t window;              /* GC_SCHED_ASYNC round 0 (and the first
+                                    tentative phase of Algorithm 2): at most
+                                    this many tiles are coloured concurrently,
+                                    claimed in vertex order; 0 = automatic (1
+                                    when most edges join nearby ids, as in a
+                                    naturally numbered mesh, else unlimited),
+                                    -1 = unlimited */
+} gc_opts;
+
+typedef struct gc_ctx gc_ctx;
+
+/* ---- library --------------------------------------------------------- */
+
+/* Static string for a status code.  Never NULL. */
+const char *gc_strerror(int status);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int gc_version(void);
+
+/* Create a context bound to CUDA device `device`: it owns the scratch
+ * memory (second colour buffer, worklists, counters) reused across calls
+ * and grown on demand.  Returns GC_OK and sets *ctx, or an error. */
+int gc_ctx_create(gc_ctx **ctx, int device);
+
+/* Free the context and its device memory (after its work finishes). */
+void gc_ctx_destroy(gc_ctx *ctx);
+
+/* ---- single graph ---------------------------------------------------- */
+
+/*
+ * Colour one graph (Sec. 3 Algorithm 3 or Sec. 2.2 Algorithm 2, per mode)
+ * and wait for the result.  row_ptr, col_idx and colors_out may each be
+ * host or device memory (host arrays are staged through the device).
+ * Uses a per-host-thread default context on the current device.
+ * colors_out: n int32 entries, written on success and on
+ * GC_ERR_NO_CONVERGENCE (the colouring at the cap).
+ * stats_out may be NULL.
+ */
+int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode,
+             int32_t *colors_out, gc_stats *stats_out);
+
+/*
+ * Enqueue the colouring of one graph on `stream` (a cudaStream_t, NULL for
+ * the legacy default stream) and return without waiting.  All pointers must
+ * be device memory that stays valid until the work completes; colors_out
+ * (n entries) also serves as the first colour buffer.  opts may be NULL.
+ * Finish with gc_ctx_stats(), which waits for the work and reports status.
+ * Returns GC_OK if the work was enqueued.
+ */
+int gc_color_async(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode,
+                   const gc_opts *opts, int32_t *colors_out, void *stream);
+
+/*
+ * Wait for the context's last enqueued colouring and report it.  Returns
+ * that colouring's status (GC_OK, GC_ERR_NO_CONVERGENCE, GC_ERR_TIMEOUT,
+ * GC_ERR_GRAPH, GC_ERR_CHECK, GC_ERR_OVERFLOW or GC_ERR_CUDA).  stats may
+ * be NULL.
+ */
+int gc_ctx_stats(gc_ctx *ctx, gc_stats *stats);
+
+/* ---- many graphs in one launch ------------------------------------------ */
+
+/*
+ * A batch of G independent graphs in one set of device arrays:
+ *   vtx_off[G+1], edge_off[G+1]: int64 prefix sums of n_g and nnz_g
+ *   row_ptr: graph g's local row pointers (n_g+1 entries, starting at 0)
+ *            begin at row_ptr + vtx_off[g] + g
+ *   col_idx: graph g's local (0-based) neighbour ids begin at
+ *            col_idx + edge_off[g]
+ * total_n = vtx_off[G] and total_nnz = edge_off[G] must be given on the
+ * host as well.  Graph g's colours land at colors_out + vtx_off[g].
+ */
+typedef struct {
+    int32_t G;
+    int64_t total_n;             /* < 2^31 */
+    int64_t total_nnz;
+    const int64_t *vtx_off;      /* device */
+    const int64_t *edge_off;     /* device */
+    const int32_t *row_ptr;      /* device */
+    const int32_t *col_idx;      /* device */
+} gc_batch;
+
+/*
+ * Colour every graph of the batch in one persistent launch (the graphs form
+ * one disjoint union; each graph's colouring, iteration count and conflict
+ * count equal those of colouring it alone in GC_SCHED_DET mode).  Per-graph
+ * results go to the optional device arrays rounds_out[G] and
+ * conflicts_out[G].  Enqueued on `stream`; finish with gc_ctx_stats().
+ */
+int gc_color_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, const gc_opts *opts,
+                   int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GC_H */

@@ -1,0 +1,83 @@
+"""Build libgc.so (the CUDA colouring library) in-tree with nvcc for sm_103a.
+
+Translation units compile in parallel into ``_build/`` and link into
+``libgc.so`` next to this file.  The library links the shared CUDA runtime so
+that, inside a PyTorch process, it binds to the runtime PyTorch already
+loaded (device pointers and streams are then interchangeable).
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libgc.so")
+SOURCES = ["gc_kernels.cu", "gc_api.cu"]
+HEADERS = [os.path.join(CSRC, "gc_internal.h"), os.path.join(INCLUDE, "gc.h")]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (cand == "nvcc" or os.path.exists(cand)):
+            return cand
+    return "nvcc"
+
+
+def _cuda_lib_dir() -> str:
+    nv = _nvcc()
+    if os.path.isabs(nv):
+        return os.path.join(os.path.dirname(os.path.dirname(nv)), "lib64")
+    return "/usr/local/cuda/lib64"
+
+
+def _stale(target: str, deps) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if needed) and return the path of libgc.so."""
+    os.makedirs(BUILD, exist_ok=True)
+    nvcc = _nvcc()
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+                     "-I", INCLUDE, "-I", CSRC]
+    objs, procs = [], []
+    for src in SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        objs.append(o)
+        if force or _stale(o, [s] + HEADERS):
+            cmd = [nvcc] + common + ["-c", s, "-o", o + ".tmp"]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((subprocess.Popen(cmd), o))
+    failed = False
+    for p, o in procs:
+        if p.wait() != 0:
+            failed = True
+        else:
+            os.replace(o + ".tmp", o)
+    if failed:
+        raise RuntimeError("nvcc failed while building libgc")
+    if force or _stale(LIB, objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
+            "-Xlinker", f"-rpath,{_cuda_lib_dir()}"]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True))

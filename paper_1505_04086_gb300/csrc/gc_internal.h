@@ -1,0 +1,93 @@
+// Internal declarations shared by the kernel and host translation units of
+// libgc.  Not part of the public ABI (include/gc.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gc.h"
+
+namespace gc {
+
+constexpr int kBlock = 256;             // threads per block of the colouring kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kT1Max = 62;              // thread path keeps colours in a 64-bit mask
+constexpr int kT2Max = 4096;            // warp path bitmap covers colours 0..kT2Max+1
+constexpr int kWarpBmWords = (kT2Max + 2) / 32 + 1;
+constexpr int kHubBmWords = 256;        // block path: 8192-colour window per pass
+constexpr int kLutShift = 10;           // batch: graph lookup per 1024 vertices
+constexpr int kRing = 4;                // round-counter ring depth
+constexpr int kStatBitmapWords = 1 << 15;  // distinct-colour bitmap: colours < 2^20
+constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
+constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
+constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
+
+enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
+enum Tie : int { TIE_LOWER = 0, TIE_HIGHER = 1, TIE_NONE = 2 };
+
+// Device-resident state of one colouring launch.  Zeroed before each launch.
+struct DevState {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int error;
+    int rounds;
+    int hub_all_count;
+    int max_color;
+    unsigned long long conflicts;
+    unsigned long long model_bytes;
+    int pass_tile[kRing];      // per-pass claim counters (tiles)
+    int pass_hub[kRing];       // per-pass claim counters (hubs)
+    int wl_count[kRing];       // per-iteration push counters (tile list)
+    int hub_count[kRing];      // per-iteration push counters (hub list)
+    unsigned long long wl_work[kRing];  // per-iteration sum of degrees pushed
+    int distinct;
+    int window;                // round-0 in-flight window in tiles (-1: unlimited)
+    unsigned long long near_lower;   // locality sample: lower neighbours within kNearIds
+    unsigned long long all_lower;    // locality sample: all lower neighbours
+};
+
+struct KParams {
+    // graph (single graph: G == 1, vtx_off/edge_off/gid_lut null)
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const int64_t *vtx_off;
+    const int64_t *edge_off;
+    const int32_t *gid_lut;
+    int32_t G;
+    int32_t n;                 // total vertices
+    int64_t nnz;               // total entries
+    // colour buffers
+    int32_t *cA;               // caller's output; first buffer
+    int32_t *cB;               // second buffer (deterministic mode)
+    // worklists (capacity n each; hub lists capacity hub_cap)
+    int32_t *wl[2];
+    int32_t *hub[2];
+    int32_t *hub_all;
+    int32_t hub_cap;
+    DevState *st;
+    int32_t *round_sizes;      // device, round_sizes_cap entries
+    int32_t round_sizes_cap;
+    int32_t *g_rounds;         // batch: per-graph iterations (device, optional)
+    unsigned long long *g_conflicts;  // batch: per-graph conflicts (device, optional)
+    uint32_t mode;
+    int32_t tie;
+    int32_t max_rounds;
+    int32_t t1, t2;
+    int32_t tile;
+    int32_t tail;
+    int32_t window;            // asynchronous round 0: tiles in flight (0 auto, -1 unlimited)
+    int32_t *done;             // per-tile completion flags of the ordered round-0 pass
+};
+
+// Launchers (gc_kernels.cu).  All return cudaSuccess or the launch error.
+cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s);
+cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm);
+size_t color_smem_bytes();
+cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, uint32_t *bitmap,
+                               int grid, cudaStream_t s);
+cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s);
+cudaError_t launch_check(const KParams &p, bool batch, int grid, cudaStream_t s);
+cudaError_t launch_build_lut(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut,
+                             cudaStream_t s);
+
+}  // namespace gc

@@ -1,0 +1,1061 @@
+// Device code of libgc: speculative First-Fit colouring for sm_103a.
+//
+// One persistent, cooperatively launched kernel runs every round of a
+// colouring (Algorithm 3, RSOC, Sec. 3; or Algorithm 2, two-phase, Sec. 2.2)
+// with a bounded grid barrier where the paper has "#pragma omp barrier".
+// Work inside a round is claimed dynamically from atomic counters in vertex
+// order (the remedy Sec. 5 proposes for SIMT lock-step: dynamic assignment of
+// vertices to threads) and split by degree:
+//   deg <= t1        one thread per vertex, forbidden colours in a 64-bit mask
+//   t1 < deg <= t2   one warp per vertex, shared-memory bitmap + ballot/ffs
+//   deg > t2         one block per vertex ("hub"), windowed shared bitmap
+// Deterministic mode keeps two colour buffers: round i reads one and writes
+// every inspected vertex's colour into the other, so each read sees the
+// colours of the end of round i-1 exactly, with one barrier per round.
+// Asynchronous mode updates one buffer in place, as the paper's threads do.
+//
+// Conflict rule (tie-break): with rows sorted, the neighbours a vertex can
+// lose to form a prefix (lower ids keep their colour) or a suffix (higher ids
+// keep theirs), so a clean vertex reads only that side of its row.
+#include <climits>
+
+#include "gc_internal.h"
+
+namespace gc {
+
+#define FULL_MASK 0xffffffffu
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+constexpr unsigned kBarrierMaxPolls = 1u << 26;
+
+// ------------------------------------------------------------------------
+// memory helpers
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_timer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+// Colour loads/stores.  Asynchronous mode reads colours that other threads
+// are writing in the same round: relaxed gpu-scope accesses, which are
+// coherent (never served from a stale L1 line).  Deterministic mode never
+// reads a buffer that is written in the same round; it still bypasses L1
+// (.cg) because the buffer was written in an earlier round of this launch.
+template <bool ASYNC>
+__device__ __forceinline__ int ld_color(const int32_t *p)
+{
+    if (ASYNC) {
+        int v;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+        return v;
+    }
+    return __ldcg(p);
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ void st_color(int32_t *p, int v)
+{
+    if (ASYNC)
+        asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    else
+        __stcg(p, v);
+}
+
+// ------------------------------------------------------------------------
+// grid barrier (bounded)
+// ------------------------------------------------------------------------
+
+// All nblocks blocks must be co-resident (cooperative launch).  A block that
+// waits longer than kBarrierTimeoutNs sets GC_EW_TIMEOUT and leaves; the
+// caller checks the error word after every barrier.
+__device__ void grid_sync(DevState *st, unsigned nblocks)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (nblocks > 1) {
+            unsigned gen = ld_acquire_u32(&st->bar_gen);
+            unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+            if (arrived == nblocks) {
+                atomicExch(&st->bar_count, 0u);
+                __threadfence();
+                st_release_u32(&st->bar_gen, gen + 1u);
+            } else {
+                unsigned long long t0 = global_timer();
+                unsigned polls = 0;
+                while (ld_acquire_u32(&st->bar_gen) == gen) {
+                    __nanosleep(64);
+                    if (++polls > kBarrierMaxPolls || global_timer() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(&st->error, GC_EW_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------
+// graph access
+// ------------------------------------------------------------------------
+
+// Row of global vertex v: entries [beg, end) of col_idx, neighbour ids are
+// nbase + col_idx[k].  For a batch, g is v's graph.
+template <bool BATCH>
+__device__ __forceinline__ void row_of(const KParams &p, int32_t v, int64_t &beg, int64_t &end,
+                                       int32_t &nbase, int32_t &g)
+{
+    if (!BATCH) {
+        beg = __ldg(p.row_ptr + v);
+        end = __ldg(p.row_ptr + v + 1);
+        nbase = 0;
+        g = 0;
+    } else {
+        int gg = __ldg(p.gid_lut + (v >> kLutShift));
+        while (gg + 1 < p.G && __ldg(p.vtx_off + gg + 1) <= (int64_t)v) ++gg;
+        const int64_t vo = __ldg(p.vtx_off + gg);
+        const int64_t eo = __ldg(p.edge_off + gg);
+        const int32_t *rp = p.row_ptr + vo + gg;
+        const int32_t lv = v - (int32_t)vo;
+        beg = eo + __ldg(rp + lv);
+        end = eo + __ldg(rp + lv + 1);
+        nbase = (int32_t)vo;
+        g = gg;
+    }
+}
+
+__device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
+{
+    return tie == TIE_LOWER ? u < v : (tie == TIE_HIGHER ? u > v : true);
+}
+
+// ------------------------------------------------------------------------
+// thread per vertex (deg <= t1 <= 62)
+// ------------------------------------------------------------------------
+
+constexpr int kUnroll = 8;
+
+// Smallest colour >= 1 not held by any neighbour (Algorithm 1 body).  With
+// deg <= 62 the answer is <= 63, so a 64-bit mask of colours 1..64 suffices.
+template <bool ASYNC>
+__device__ __forceinline__ int ff_thread(const KParams &p, int64_t beg, int deg, int32_t nbase,
+                                         const int32_t *R)
+{
+    unsigned long long mask = 0;
+    for (int i = 0; i < deg; i += kUnroll) {
+        int u[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) u[q] = (i + q < deg) ? nbase + __ldg(p.col_idx + beg + i + q) : -1;
+        int c[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) c[q] = (u[q] >= 0) ? ld_color<ASYNC>(R + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            unsigned b = (unsigned)(c[q] - 1);
+            if (b < 64u) mask |= 1ull << b;
+        }
+    }
+    return __ffsll((long long)~mask);
+}
+
+// Is some neighbour on v's tie side coloured cv?  t = tie-side entries seen
+// (the whole tie side unless stop_early ended the scan at a conflict).
+template <bool ASYNC>
+__device__ __forceinline__ bool detect_thread(const KParams &p, int32_t v, int64_t beg, int64_t end,
+                                              int32_t nbase, const int32_t *R, int cv,
+                                              bool stop_early, int &t)
+{
+    const int deg = (int)(end - beg);
+    const int tie = p.tie;
+    bool def = false;
+    t = 0;
+    for (int i = 0; i < deg; i += kUnroll) {
+        int u[kUnroll];
+        bool side[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            const int ii = i + q;
+            const bool in = ii < deg;
+            const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
+            u[q] = in ? nbase + __ldg(p.col_idx + k) : 0;
+            side[q] = in && on_tie_side(tie, u[q], v);
+        }
+        int c[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q)
+            if (side[q]) {
+                ++t;
+                def |= (c[q] == cv);
+            }
+        if (tie != TIE_NONE && !side[kUnroll - 1]) break;  // sorted: tie side ended
+        if (def && stop_early) break;
+    }
+    return def;
+}
+
+// One vertex, one thread.  Returns true if v must join the next worklist.
+// Byte model accounting goes to mb (see gc.h, gc_stats.model_bytes).
+template <bool ASYNC>
+__device__ __forceinline__ bool vertex_thread(const KParams &p, int op, int32_t v, int64_t beg, int64_t end,
+                                              int32_t nbase, const int32_t *R, int32_t *W, bool implicit,
+                                              long long &mb)
+{
+    const int deg = (int)(end - beg);
+    mb += (implicit ? 0 : 4) + 8;
+    if (op == OP_TENT) {
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(p, beg, deg, nbase, R));
+        mb += 8ll * deg + 4;
+        return false;
+    }
+    const int cv = ld_color<ASYNC>(R + v);
+    mb += 4;
+    int t;
+    const bool d = detect_thread<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, t);
+    if (op == OP_DETECT) {
+        if (!ASYNC) st_color<false>(p.cA + v, cv);  // two-phase: bring buffer A up to date
+        mb += 8ll * t + (d ? 4 : 0);
+        return d;
+    }
+    if (d) {
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(p, beg, deg, nbase, R));
+        mb += 8ll * deg + 8;
+    } else {
+        if (W != R) st_color<ASYNC>(W + v, cv);  // snapshot rounds: carry the colour over
+        mb += 8ll * t;
+    }
+    return d;
+}
+
+// ------------------------------------------------------------------------
+// warp per vertex (t1 < deg <= t2 <= kT2Max)
+// ------------------------------------------------------------------------
+
+template <bool ASYNC>
+__device__ int ff_warp(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R,
+                       uint32_t *bm, int lane)
+{
+    const int nwords = (deg + 1) / 32 + 1;  // bits for colours 0..deg+1
+    __syncwarp();
+    for (int w = lane; w < nwords; w += 32) bm[w] = (w == 0) ? 1u : 0u;  // colour 0 is not a colour
+    __syncwarp();
+    for (int i0 = 0; i0 < deg; i0 += 32 * 4) {
+        int c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * 32 + lane;
+            c[q] = (i < deg) ? ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i)) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if ((unsigned)c[q] <= (unsigned)(deg + 1)) atomicOr(&bm[c[q] >> 5], 1u << (c[q] & 31));
+    }
+    __syncwarp();
+    for (int w0 = 0; w0 < nwords; w0 += 32) {
+        const int w = w0 + lane;
+        const uint32_t freeb = (w < nwords) ? ~bm[w] : 0u;
+        const unsigned bal = __ballot_sync(FULL_MASK, freeb != 0u);
+        if (bal) {
+            const int src = __ffs(bal) - 1;
+            const uint32_t fb = __shfl_sync(FULL_MASK, freeb, src);
+            return (w0 + src) * 32 + __ffs(fb) - 1;
+        }
+    }
+    return deg + 1;  // not reached: one of 1..deg+1 is always free
+}
+
+template <bool ASYNC>
+__device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                            const int32_t *R, int cv, bool stop_early, int lane, int &t_total)
+{
+    const int deg = (int)(end - beg);
+    const int tie = p.tie;
+    bool def = false;
+    int t = 0;
+    for (int i0 = 0; i0 < deg; i0 += 32) {
+        const int ii = i0 + lane;
+        const bool in = ii < deg;
+        const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
+        const int32_t u = in ? nbase + __ldg(p.col_idx + k) : 0;
+        const bool side = in && on_tie_side(tie, u, v);
+        if (side) {
+            ++t;
+            if (ld_color<ASYNC>(R + u) == cv) def = true;
+        }
+        const unsigned sides = __ballot_sync(FULL_MASK, side);
+        const bool any_def = __any_sync(FULL_MASK, def);
+        if (tie != TIE_NONE && !(sides >> 31)) break;
+        if (any_def && stop_early) break;
+    }
+    t_total = __reduce_add_sync(FULL_MASK, t);
+    return __any_sync(FULL_MASK, def);
+}
+
+template <bool ASYNC>
+__device__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                            const int32_t *R, int32_t *W, bool implicit, long long &mb, uint32_t *bm,
+                            int lane)
+{
+    const int deg = (int)(end - beg);
+    long long add = (implicit ? 0 : 4) + 8;
+    bool d = false;
+    if (op == OP_TENT) {
+        const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, bm, lane);
+        if (lane == 0) st_color<ASYNC>(W + v, c);
+        add += 8ll * deg + 4;
+    } else {
+        const int cv = ld_color<ASYNC>(R + v);
+        add += 4;
+        int t;
+        d = detect_warp<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, lane, t);
+        if (op == OP_DETECT) {
+            if (!ASYNC && lane == 0) st_color<false>(p.cA + v, cv);
+            add += 8ll * t + (d ? 4 : 0);
+        } else if (d) {
+            const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, bm, lane);
+            if (lane == 0) st_color<ASYNC>(W + v, c);
+            add += 8ll * deg + 8;
+        } else {
+            if (W != R && lane == 0) st_color<ASYNC>(W + v, cv);
+            add += 8ll * t;
+        }
+    }
+    if (lane == 0) mb += add;
+    return d;
+}
+
+// ------------------------------------------------------------------------
+// block per vertex (deg > t2)
+// ------------------------------------------------------------------------
+
+struct Shared {
+    uint32_t warp_bm[kWarps][kWarpBmWords];
+    uint32_t hub_bm[kHubBmWords];
+    int first;
+    int tcount;
+    int claim;
+    int pad;
+};
+
+template <bool ASYNC>
+__device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R, Shared &sh)
+{
+    constexpr int kWin = kHubBmWords * 32;
+    for (int base = 0;; base += kWin) {
+        for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) sh.hub_bm[w] = 0u;
+        if (threadIdx.x == 0) sh.first = INT_MAX;
+        __syncthreads();
+        for (int i = threadIdx.x; i < deg; i += kBlock) {
+            const int c = ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i));
+            const int d = c - base;
+            if (d >= 0 && d < kWin) atomicOr(&sh.hub_bm[d >> 5], 1u << (d & 31));
+        }
+        __syncthreads();
+        for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) {
+            uint32_t f = ~sh.hub_bm[w];
+            if (w == 0 && base == 0) f &= ~1u;  // colour 0 is not a colour
+            if (f) atomicMin(&sh.first, w * 32 + __ffs(f) - 1);
+        }
+        __syncthreads();
+        const int first = sh.first;
+        __syncthreads();
+        if (first != INT_MAX) return base + first;
+        if (base > deg + 1) return deg + 1;  // not reached
+    }
+}
+
+template <bool ASYNC>
+__device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                             const int32_t *R, int cv, bool stop_early, Shared &sh, int &t_total)
+{
+    const int deg = (int)(end - beg);
+    const int tie = p.tie;
+    bool def = false;
+    int t = 0;
+    if (threadIdx.x == 0) sh.tcount = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < deg; i0 += kBlock) {
+        const int ii = i0 + threadIdx.x;
+        const bool in = ii < deg;
+        const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
+        const int32_t u = in ? nbase + __ldg(p.col_idx + k) : 0;
+        const bool side = in && on_tie_side(tie, u, v);
+        if (side) {
+            ++t;
+            if (ld_color<ASYNC>(R + u) == cv) def = true;
+        }
+        const int more = __syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side : 0);
+        const int any_def = __syncthreads_or((int)def);
+        if (tie != TIE_NONE && !more) break;
+        if (any_def && stop_early) break;
+    }
+    if (t) atomicAdd(&sh.tcount, t);
+    const int any = __syncthreads_or((int)def);
+    t_total = sh.tcount;
+    __syncthreads();
+    return any != 0;
+}
+
+template <bool ASYNC>
+__device__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                             const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh)
+{
+    const int deg = (int)(end - beg);
+    long long add = (implicit ? 0 : 4) + 8;
+    bool d = false;
+    if (op == OP_TENT) {
+        const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, sh);
+        if (threadIdx.x == 0) st_color<ASYNC>(W + v, c);
+        add += 8ll * deg + 4;
+    } else {
+        const int cv = ld_color<ASYNC>(R + v);
+        add += 4;
+        int t;
+        d = detect_block<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, sh, t);
+        if (op == OP_DETECT) {
+            if (!ASYNC && threadIdx.x == 0) st_color<false>(p.cA + v, cv);
+            add += 8ll * t + (d ? 4 : 0);
+        } else if (d) {
+            const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, sh);
+            if (threadIdx.x == 0) st_color<ASYNC>(W + v, c);
+            add += 8ll * deg + 8;
+        } else {
+            if (W != R && threadIdx.x == 0) st_color<ASYNC>(W + v, cv);
+            add += 8ll * t;
+        }
+    }
+    if (threadIdx.x == 0) mb += add;
+    return d;
+}
+
+// ------------------------------------------------------------------------
+// ordered tentative colouring of a chunk of 32 consecutive ids (round 0)
+// ------------------------------------------------------------------------
+
+// The 32 lanes colour ids cbase..cbase+31 as sequential First-Fit would:
+// lane k sees the final colours of every lower lane it is adjacent to (they
+// are resolved in lane order through shuffles) and the current colours of
+// every neighbour outside the chunk.  This removes the lock-step tie of
+// Sec. 5 / Fig. 7 inside a warp.  Hub ids (coloured before the tiles) count
+// as outside; warp-path ids are coloured afterwards and see all lanes.
+template <bool BATCH>
+__device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C, long long &mb, uint32_t *bm,
+                                   int lane)
+{
+    const long long vi = cbase + lane;
+    int32_t v = vi < p.n ? (int32_t)vi : -1;
+    int64_t beg = 0, end = 0;
+    int32_t nbase = 0, g = 0;
+    if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
+    const int deg = (int)(end - beg);
+    const bool hub = v >= 0 && deg > p.t2;
+    const bool mid = v >= 0 && !hub && deg > p.t1;
+    const bool thr = v >= 0 && !hub && !mid;
+    const unsigned hubmask = __ballot_sync(FULL_MASK, hub);
+    const unsigned midmask = __ballot_sync(FULL_MASK, mid);
+    unsigned long long ext = 0;
+    unsigned low = 0;
+    if (thr) {
+        for (int i = 0; i < deg; i += kUnroll) {
+            int u[kUnroll];
+            bool outside[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                u[q] = (i + q < deg) ? nbase + __ldg(p.col_idx + beg + i + q) : -1;
+                const long long d = (long long)u[q] - cbase;
+                const bool inside = u[q] >= 0 && d >= 0 && d < 32 && !((hubmask >> d) & 1u);
+                if (inside && u[q] < v && !((midmask >> d) & 1u)) low |= 1u << d;
+                outside[q] = u[q] >= 0 && !inside;
+            }
+            int c[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) c[q] = outside[q] ? ld_color<true>(C + u[q]) : 0;
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const unsigned b = (unsigned)(c[q] - 1);
+                if (b < 64u) ext |= 1ull << b;
+            }
+        }
+    }
+    int mine = 0;
+    for (int k = 0; k < 32; ++k) {
+        if (lane == k && thr) mine = __ffsll((long long)~ext);
+        const int ck = __shfl_sync(FULL_MASK, mine, k);
+        if ((low >> k) & 1u) ext |= 1ull << (ck - 1);
+    }
+    if (thr) {
+        st_color<true>(C + v, mine);
+        mb += 8 + 8ll * deg + 4;
+    }
+    __syncwarp();
+    unsigned mm = midmask;
+    while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int32_t vv = __shfl_sync(FULL_MASK, v, src);
+        const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
+        const int64_t ee = __shfl_sync(FULL_MASK, end, src);
+        const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
+        vertex_warp<true>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane);
+    }
+}
+
+// Wait (bounded) until tile t of the ordered pass has been published.
+__device__ void wait_tile_done(const KParams &p, long long t, int lane)
+{
+    if (lane == 0) {
+        const unsigned *f = reinterpret_cast<const unsigned *>(p.done + t);
+        unsigned long long t0 = global_timer();
+        unsigned polls = 0;
+        while (ld_acquire_u32(f) == 0u) {
+            __nanosleep(32);
+            if (++polls > kBarrierMaxPolls || global_timer() - t0 > kBarrierTimeoutNs) {
+                atomicOr(&p.st->error, GC_EW_TIMEOUT);
+                break;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ void publish_tile_done(const KParams &p, long long t, int lane)
+{
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        st_release_u32(reinterpret_cast<unsigned *>(p.done + t), 1u);
+    }
+}
+
+// ------------------------------------------------------------------------
+// one pass over a worklist
+// ------------------------------------------------------------------------
+
+template <bool BATCH>
+__device__ __forceinline__ void note_push_graph(const KParams &p, int32_t g, int it)
+{
+    if (BATCH) {
+        if (p.g_conflicts) atomicAdd(p.g_conflicts + g, 1ull);
+        if (p.g_rounds) atomicMax(p.g_rounds + g, it + 1);
+    }
+}
+
+struct PassIn {
+    bool implicit;             // worklist is all of V (ids 0..n-1)
+    const int32_t *wl;         // explicit tile worklist
+    int32_t n;                 // its length (or n for implicit)
+    const int32_t *hub;        // hub worklist
+    int32_t hn;
+};
+
+// Runs `op` over the hubs (block per vertex) and then the tiles (warp per
+// 32 entries) of `in`.  Vertices found defective are appended to the
+// worklists of iteration `it` when `push` is set.
+template <bool ASYNC, bool BATCH>
+__device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
+                         const int32_t *R, int32_t *W, bool push, long long &mb, int window = -1)
+{
+    DevState *st = p.st;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->pass_tile[(q + 2) & (kRing - 1)] = 0;
+        st->pass_hub[(q + 2) & (kRing - 1)] = 0;
+    }
+    int *out_wl = p.wl[it & 1];
+    int *out_hub = p.hub[it & 1];
+
+    // hubs: one block per vertex, longest tasks first
+    if (in.hn > 0) {
+        int *claim = &st->pass_hub[q & (kRing - 1)];
+        for (;;) {
+            if (threadIdx.x == 0) sh.claim = atomicAdd(claim, 1);
+            __syncthreads();
+            const int h = sh.claim;
+            __syncthreads();
+            if (h >= in.hn) break;
+            const int32_t v = __ldcg(in.hub + h);
+            int64_t beg, end;
+            int32_t nbase, g;
+            row_of<BATCH>(p, v, beg, end, nbase, g);
+            const bool d = vertex_block<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh);
+            if (push && d && threadIdx.x == 0) {
+                atomicAdd(&st->wl_work[it & (kRing - 1)], (unsigned long long)(end - beg));
+                const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
+                if (idx < p.hub_cap) __stcg(out_hub + idx, v);
+                else atomicOr(&st->error, GC_EW_OVERFLOW);
+                note_push_graph<BATCH>(p, g, it);
+            }
+        }
+    }
+
+    // tiles: one warp per group of `tile` consecutive worklist entries
+    int *claim = &st->pass_tile[q & (kRing - 1)];
+    if (ASYNC && op == OP_TENT && in.implicit) {
+        // Ordered tentative pass over V: tiles claimed in id order, lanes
+        // resolved in id order, at most `window` tiles in flight.
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(claim, 1);
+            t = __shfl_sync(FULL_MASK, t, 0);
+            const long long base = (long long)t * p.tile;
+            if (base >= in.n) break;
+            if (window > 0 && t >= window) wait_tile_done(p, t - window, lane);
+            for (int j = 0; j < p.tile && base + j < in.n; j += 32)
+                chunk_tent_ordered<BATCH>(p, base + j, W, mb, sh.warp_bm[wid], lane);
+            if (window > 0) publish_tile_done(p, t, lane);
+        }
+        return;
+    }
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(claim, 1);
+        t = __shfl_sync(FULL_MASK, t, 0);
+        const long long base = (long long)t * p.tile;
+        if (base >= in.n) break;
+        for (int j = 0; j < p.tile && base + j < in.n; j += 32) {
+            const long long idx = base + j + lane;
+            int32_t v = -1;
+            if (idx < in.n) v = in.implicit ? (int32_t)idx : __ldcg(in.wl + idx);
+            int64_t beg = 0, end = 0;
+            int32_t nbase = 0, g = 0;
+            if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
+            const int deg = (int)(end - beg);
+            if (in.implicit && deg > p.t2) v = -1;  // hubs went through the block phase
+            const bool mid = v >= 0 && deg > p.t1;
+            bool d = false;
+            if (v >= 0 && !mid) d = vertex_thread<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb);
+            unsigned mm = __ballot_sync(FULL_MASK, mid);
+            while (mm) {
+                const int src = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const int32_t vv = __shfl_sync(FULL_MASK, v, src);
+                const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
+                const int64_t ee = __shfl_sync(FULL_MASK, end, src);
+                const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
+                const bool dd = vertex_warp<ASYNC>(p, op, vv, bb, ee, nb, R, W, in.implicit, mb,
+                                                   sh.warp_bm[wid], lane);
+                if (lane == src) d = dd;
+            }
+            if (push) {
+                const unsigned m = __ballot_sync(FULL_MASK, d);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    unsigned long long work = d ? (unsigned long long)deg : 0ull;
+                    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(FULL_MASK, work, o);
+                    int ob = 0;
+                    if (lane == leader) {
+                        ob = atomicAdd(&st->wl_count[it & (kRing - 1)], __popc(m));
+                        atomicAdd(&st->wl_work[it & (kRing - 1)], work);
+                    }
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (d) {
+                        const int o = ob + __popc(m & ((1u << lane) - 1u));
+                        if (o < p.n) __stcg(out_wl + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                        note_push_graph<BATCH>(p, g, it);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// the colouring kernel
+// ------------------------------------------------------------------------
+
+template <bool ASYNC, bool BATCH>
+__global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
+{
+    __shared__ Shared sh;
+    DevState *st = p.st;
+    const int lane = threadIdx.x & 31;
+    const bool twop = (p.mode & GC_ALG_TWO_PHASE) != 0;
+    // Snapshot rounds: deterministic mode, or asynchronous round 0 followed
+    // by round-synchronous repair rounds (GC_REPAIR_SNAPSHOT, RSOC only).
+    const bool snap = !twop && (!ASYNC || (p.mode & GC_REPAIR_SNAPSHOT) != 0);
+    unsigned nbl = gridDim.x;
+    long long mb = 0;
+
+    if (ld_volatile(&st->error) == 0) {
+        // Prologue: degree binning of V (hub list) and colour initialisation.
+        // Deterministic round 0 colours every vertex from a snapshot in which
+        // nothing is coloured yet, so every vertex gets colour 1.
+        const long long stride = (long long)gridDim.x * kBlock;
+        for (long long b0 = (long long)blockIdx.x * kBlock; b0 < p.n; b0 += stride) {
+            const long long vi = b0 + threadIdx.x;
+            bool hub = false;
+            const int32_t v = (int32_t)vi;
+            if (vi < p.n) {
+                int64_t beg, end;
+                int32_t nbase, g;
+                row_of<BATCH>(p, v, beg, end, nbase, g);
+                hub = (end - beg) > p.t2;
+                st_color<false>(p.cA + v, ASYNC ? 0 : 1);
+                if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
+                if (!ASYNC) mb += 4;
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, hub);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int ob = 0;
+                if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
+                ob = __shfl_sync(FULL_MASK, ob, leader);
+                if (hub) {
+                    const int o = ob + __popc(m & ((1u << lane) - 1u));
+                    if (o < p.hub_cap) __stcg(p.hub_all + o, v);
+                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+                }
+            }
+        }
+        if (BATCH && p.g_rounds)
+            for (long long g = (long long)blockIdx.x * kBlock + threadIdx.x; g < p.G; g += stride)
+                p.g_rounds[g] = (__ldg(p.vtx_off + g + 1) > __ldg(p.vtx_off + g)) ? 1 : 0;
+        if (ASYNC) {
+            // Flags of the ordered round-0 pass, and (automatic window) a
+            // sample of how far lower neighbours sit in id from their vertex.
+            const long long ntiles = ((long long)p.n + p.tile - 1) / p.tile;
+            for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < ntiles; t += stride)
+                p.done[t] = 0;
+            if (p.window == 0) {
+                unsigned long long near = 0, all = 0;
+                for (long long vi = ((long long)blockIdx.x * kBlock + threadIdx.x) * kLocalitySample; vi < p.n;
+                     vi += stride * kLocalitySample) {
+                    int64_t beg, end;
+                    int32_t nbase, g;
+                    row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, g);
+                    for (int64_t k = beg; k < end; ++k) {
+                        const int32_t u = nbase + __ldg(p.col_idx + k);
+                        if (u >= (int32_t)vi) break;
+                        ++all;
+                        near += ((int32_t)vi - u) < kNearIds;
+                    }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    near += __shfl_down_sync(FULL_MASK, near, o);
+                    all += __shfl_down_sync(FULL_MASK, all, o);
+                }
+                if (lane == 0 && all) {
+                    atomicAdd(&st->near_lower, near);
+                    atomicAdd(&st->all_lower, all);
+                }
+            }
+        }
+        grid_sync(st, nbl);
+
+        bool alive = ld_volatile(&st->error) == 0;
+        const int hub_all_n = ld_volatile(&st->hub_all_count);
+        int q = 0;
+        PassIn in{true, nullptr, p.n, p.hub_all, hub_all_n};
+        int window = p.window;
+        if (ASYNC && window == 0) {
+            // Ids of a naturally numbered mesh are local: neighbours would be
+            // coloured concurrently unless tiles go strictly in order.
+            const unsigned long long near = *(volatile unsigned long long *)&st->near_lower;
+            const unsigned long long all = *(volatile unsigned long long *)&st->all_lower;
+            window = (all > 0 && 2 * near >= all) ? 1 : -1;
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->window = window;
+        }
+
+        // Asynchronous round 0 (Algorithm 3): tentative colouring of all of V.
+        if (alive && ASYNC && !twop) {
+            run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, 0, in, p.cA, p.cA, false, mb, window);
+            grid_sync(st, nbl);
+            alive = ld_volatile(&st->error) == 0;
+        }
+
+        int32_t *R = p.cA;
+        int32_t *W = snap ? p.cB : p.cA;
+        int32_t *last_written = p.cA;
+        bool copy_back = false;
+        for (int it = 1; alive; ++it) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->wl_count[(it + 2) & (kRing - 1)] = 0;
+                st->hub_count[(it + 2) & (kRing - 1)] = 0;
+                st->wl_work[(it + 2) & (kRing - 1)] = 0;
+            }
+            if (twop) {
+                // Algorithm 2: phase 1 tentative colouring of U (in
+                // deterministic mode iteration 1's phase 1 is the fill of
+                // the prologue), barrier, phase 2 detection, barrier.
+                if (ASYNC || it > 1) {
+                    run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false, mb,
+                                           window);
+                    grid_sync(st, nbl);
+                    if (ld_volatile(&st->error)) break;
+                }
+                run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb);
+            } else {
+                // Algorithm 3: fused detect-and-recolour over U.
+                run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb);
+                last_written = W;
+            }
+            grid_sync(st, nbl);
+            if (ld_volatile(&st->error)) {
+                copy_back = true;
+                break;
+            }
+            const int nl = ld_volatile(&st->wl_count[it & (kRing - 1)]);
+            const int nh = ld_volatile(&st->hub_count[it & (kRing - 1)]);
+            const int tot = nl + nh;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                st->rounds = it;
+                st->conflicts += (unsigned long long)tot;
+                if (p.round_sizes && it - 1 < p.round_sizes_cap) p.round_sizes[it - 1] = tot;
+            }
+            if (snap) {
+                int32_t *t = R;
+                R = W;
+                W = t;
+            }
+            if (tot == 0) break;
+            if (it >= p.max_rounds) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->error, GC_EW_NO_CONVERGENCE);
+                copy_back = true;
+                break;
+            }
+            in = PassIn{false, p.wl[it & 1], nl, p.hub[it & 1], nh};
+            const unsigned long long work = *(volatile unsigned long long *)&st->wl_work[it & (kRing - 1)];
+            if (nbl > 1 && tot <= p.tail && work <= (unsigned long long)p.tail * kTailWorkPerVertex) {
+                // Few vertices left: block 0 finishes alone with block-local
+                // barriers; the others leave.
+                if (blockIdx.x != 0) {
+                    alive = false;
+                    break;
+                }
+                nbl = 1;
+            }
+        }
+        // Deterministic RSOC stopped early (cap or error): the latest colours
+        // may sit in the second buffer.  On normal termination both buffers
+        // hold the final colouring.
+        if (alive && copy_back && snap && last_written != p.cA) {
+            const long long s2 = (long long)nbl * kBlock;
+            for (long long v = (long long)blockIdx.x * kBlock + threadIdx.x; v < p.n; v += s2)
+                __stcg(p.cA + v, __ldcg(p.cB + v));
+        }
+    }
+
+    // flush the byte-model counter
+    for (int o = 16; o > 0; o >>= 1) mb += __shfl_down_sync(FULL_MASK, mb, o);
+    if (lane == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
+}
+
+// ------------------------------------------------------------------------
+// auxiliary kernels
+// ------------------------------------------------------------------------
+
+// Largest colour and presence bitmap of colours (for the distinct count).
+__global__ void color_stats_kernel(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
+{
+    int mx = 0;
+    unsigned long long low = 0;  // colours 0..63, OR-reduced per warp
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = __ldcg(c + i);
+        mx = max(mx, x);
+        if (x >= 0 && x < 64) low |= 1ull << x;
+        else if (x >= 64 && x < kStatBitmapWords * 32) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_down_sync(FULL_MASK, mx, o));
+        low |= __shfl_down_sync(FULL_MASK, low, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(&st->max_color, mx);
+        if (low & 0xffffffffull) atomicOr(&bitmap[0], (uint32_t)low);
+        if (low >> 32) atomicOr(&bitmap[1], (uint32_t)(low >> 32));
+    }
+}
+
+__global__ void popcount_kernel(const uint32_t *bitmap, DevState *st)
+{
+    __shared__ int acc;
+    if (threadIdx.x == 0) acc = 0;
+    __syncthreads();
+    int s = 0;
+    for (int w = threadIdx.x; w < kStatBitmapWords; w += blockDim.x) {
+        uint32_t x = bitmap[w];
+        if (w == 0) x &= ~1u;  // colour 0 is not a colour
+        s += __popc(x);
+    }
+    atomicAdd(&acc, s);
+    __syncthreads();
+    if (threadIdx.x == 0) st->distinct = acc;
+}
+
+// Input well-formedness: row pointers, range, no self-loop, strictly
+// increasing rows and a mirror entry for every entry.
+template <bool BATCH>
+__global__ void validate_kernel(KParams p)
+{
+    bool bad = false;
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < p.n && !bad;
+         vi += (long long)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)vi;
+        int64_t beg, end;
+        int32_t nbase, g;
+        row_of<BATCH>(p, v, beg, end, nbase, g);
+        int64_t gn = p.n, lo_e = 0, hi_e = LLONG_MAX;
+        if (BATCH) {
+            gn = __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g);
+            lo_e = __ldg(p.edge_off + g);
+            hi_e = __ldg(p.edge_off + g + 1);
+            if (v == nbase && __ldg(p.row_ptr + nbase + g) != 0) bad = true;
+        }
+        if (!BATCH) {
+            hi_e = p.nnz;
+            if (v == 0 && beg != 0) bad = true;
+        }
+        if (beg > end || beg < lo_e || end > hi_e) { bad = true; break; }
+        if (v - nbase == gn - 1 && end != hi_e) { bad = true; break; }  // last row ends at nnz
+        for (int64_t k = beg; k < end && !bad; ++k) {
+            const int32_t lu = __ldg(p.col_idx + k);
+            if (lu < 0 || lu >= gn) { bad = true; break; }
+            const int32_t u = nbase + lu;
+            if (u == v) bad = true;
+            if (k > beg && __ldg(p.col_idx + k - 1) >= lu) bad = true;
+            if (bad) break;
+            int64_t ub, ue;
+            int32_t unb, ug;
+            row_of<BATCH>(p, u, ub, ue, unb, ug);
+            const int32_t lv = v - nbase;
+            int64_t lo = ub, hi = ue;  // binary search for v in u's row
+            bool found = false;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                const int32_t x = __ldg(p.col_idx + mid);
+                if (x == lv) { found = true; break; }
+                if (x < lv) lo = mid + 1; else hi = mid;
+            }
+            if (!found) bad = true;
+        }
+    }
+    if (bad) atomicOr(&p.st->error, GC_EW_GRAPH);
+}
+
+// Result check: 1 <= c(v) <= deg(v)+1 and no neighbour shares c(v).
+template <bool BATCH>
+__global__ void check_kernel(KParams p)
+{
+    bool bad = false;
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < p.n && !bad;
+         vi += (long long)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)vi;
+        int64_t beg, end;
+        int32_t nbase, g;
+        row_of<BATCH>(p, v, beg, end, nbase, g);
+        const int cv = __ldcg(p.cA + v);
+        if (cv < 1 || cv > (int)(end - beg) + 1) bad = true;
+        for (int64_t k = beg; k < end && !bad; ++k)
+            if (__ldcg(p.cA + nbase + __ldg(p.col_idx + k)) == cv) bad = true;
+    }
+    if (bad) atomicOr(&p.st->error, GC_EW_CHECK);
+}
+
+// Batch: graph of the first vertex of every 2^kLutShift-vertex chunk.
+__global__ void build_lut_kernel(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut)
+{
+    const long long chunks = ((long long)n + (1 << kLutShift) - 1) >> kLutShift;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int64_t x = c << kLutShift;
+        int lo = 0, hi = G - 1;  // largest g with vtx_off[g] <= x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (vtx_off[mid] <= x) lo = mid; else hi = mid - 1;
+        }
+        lut[c] = lo;
+    }
+}
+
+// ------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------
+
+template <bool A, bool B>
+static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, color_kernel<A, B>, p);
+}
+
+cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s)
+{
+    if (async) return batch ? launch_one<true, true>(p, grid, s) : launch_one<true, false>(p, grid, s);
+    return batch ? launch_one<false, true>(p, grid, s) : launch_one<false, false>(p, grid, s);
+}
+
+cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm)
+{
+    const void *f = async ? (batch ? (const void *)color_kernel<true, true> : (const void *)color_kernel<true, false>)
+                          : (batch ? (const void *)color_kernel<false, true> : (const void *)color_kernel<false, false>);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, 0);
+}
+
+size_t color_smem_bytes() { return sizeof(Shared); }
+
+cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, uint32_t *bitmap, int grid,
+                               cudaStream_t s)
+{
+    color_stats_kernel<<<grid, 256, 0, s>>>(colors, n, st, bitmap);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    popcount_kernel<<<1, 1024, 0, s>>>(bitmap, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s)
+{
+    if (batch) validate_kernel<true><<<grid, 256, 0, s>>>(p);
+    else validate_kernel<false><<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check(const KParams &p, bool batch, int grid, cudaStream_t s)
+{
+    if (batch) check_kernel<true><<<grid, 256, 0, s>>>(p);
+    else check_kernel<false><<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_lut(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut, cudaStream_t s)
+{
+    const long long chunks = ((long long)n + (1 << kLutShift) - 1) >> kLutShift;
+    long long blocks = (chunks + 255) / 256;
+    const int grid = (int)(blocks < 1 ? 1 : (blocks > 4096 ? 4096 : blocks));
+    build_lut_kernel<<<grid, 256, 0, s>>>(vtx_off, G, n, lut);
+    return cudaGetLastError();
+}
+
+}  // namespace gc

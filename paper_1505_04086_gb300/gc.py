@@ -1,0 +1,305 @@
+"""ctypes binding of libgc (include/gc.h): argument marshalling only.
+
+Every step of the colouring runs in the CUDA library; this module converts
+torch tensors / numpy arrays to pointers and structs and back.  It raises if
+libgc.so has not been built: there is no CPU fallback.
+
+The entry points keep the C names (gc_color, gc_color_async, gc_ctx_stats,
+gc_color_batch, ...); :class:`Context` is a small convenience wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+# status codes
+GC_OK = 0
+GC_PENDING = 1
+GC_ERR_ARG = -1
+GC_ERR_GRAPH = -2
+GC_ERR_OOM = -3
+GC_ERR_BUDGET = -4
+GC_ERR_NO_CONVERGENCE = -5
+GC_ERR_TIMEOUT = -6
+GC_ERR_CUDA = -7
+GC_ERR_OVERFLOW = -8
+GC_ERR_CHECK = -9
+GC_ERR_NOT_FOUND = -10
+
+# mode bits
+GC_ALG_RSOC = 0
+GC_ALG_TWO_PHASE = 1
+GC_SCHED_DET = 0
+GC_SCHED_ASYNC = 2
+GC_TIE_LOWER_KEEPS = 0
+GC_TIE_HIGHER_KEEPS = 4
+GC_VALIDATE = 8
+GC_CHECKED = 16
+GC_DEBUG_NO_TIEBREAK = 32
+GC_NO_COLOR_STATS = 64
+GC_REPAIR_SNAPSHOT = 128
+
+# error word bits
+GC_EW_TIMEOUT = 1
+GC_EW_NO_CONVERGENCE = 2
+GC_EW_OVERFLOW = 4
+GC_EW_GRAPH = 8
+GC_EW_CHECK = 16
+
+
+class gc_csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class gc_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("colors", ctypes.c_int32),
+                ("conflicts", ctypes.c_int64), ("distinct_colors", ctypes.c_int32),
+                ("error_word", ctypes.c_int32), ("model_bytes", ctypes.c_int64),
+                ("elapsed_ms", ctypes.c_float), ("round_sizes", ctypes.c_void_p),
+                ("round_sizes_cap", ctypes.c_int32)]
+
+
+class gc_opts(ctypes.Structure):
+    _fields_ = [("max_rounds", ctypes.c_int32), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("tail", ctypes.c_int32), ("window", ctypes.c_int32)]
+
+
+class gc_batch(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_int32), ("total_n", ctypes.c_int64), ("total_nnz", ctypes.c_int64),
+                ("vtx_off", ctypes.c_void_p), ("edge_off", ctypes.c_void_p),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+# Every function the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+_SIGS = {
+    "gc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "gc_version": (ctypes.c_int, []),
+    "gc_ctx_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int]),
+    "gc_ctx_destroy": (None, [_P]),
+    "gc_color": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                _P, ctypes.POINTER(gc_stats)]),
+    "gc_color_async": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_uint32, ctypes.POINTER(gc_opts), _P, _P]),
+    "gc_ctx_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
+    "gc_color_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32,
+                                      ctypes.POINTER(gc_opts), _P, _P, _P, _P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgc.so.  Raises if it is missing (run the package build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgc.so not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_1505_04086_gb300._build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+class GCError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {gc_strerror(status)} ({status})")
+
+
+def gc_strerror(status: int) -> str:
+    return load().gc_strerror(int(status)).decode()
+
+
+def gc_version() -> int:
+    return int(load().gc_version())
+
+
+# ---------------------------------------------------------------- marshalling
+
+def _ptr(x) -> int:
+    """Raw address of a torch tensor or numpy array (None -> 0)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return int(x.ctypes.data)
+    raise TypeError(f"expected a torch tensor or numpy array, got {type(x)}")
+
+
+def _check_i32(x, name):
+    dt = getattr(x, "dtype", None)
+    if str(dt) not in ("int32", "torch.int32"):
+        raise TypeError(f"{name} must be int32, got {dt}")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _opts(opts) -> gc_opts | None:
+    if opts is None:
+        return None
+    if isinstance(opts, gc_opts):
+        return opts
+    o = gc_opts()
+    for k, v in dict(opts).items():
+        setattr(o, k, int(v))
+    return o
+
+
+def stats_dict(s: gc_stats, round_sizes=None) -> dict:
+    d = {"rounds": s.rounds, "colors": s.colors, "conflicts": s.conflicts,
+         "distinct_colors": s.distinct_colors, "error_word": s.error_word,
+         "model_bytes": s.model_bytes, "elapsed_ms": float(s.elapsed_ms)}
+    if round_sizes is not None:
+        d["round_sizes"] = round_sizes[: min(s.rounds, len(round_sizes))].copy()
+    return d
+
+
+def gc_ctx_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    rc = load().gc_ctx_create(ctypes.byref(h), int(device))
+    if rc != GC_OK:
+        raise GCError(rc, "gc_ctx_create")
+    return int(h.value)
+
+
+def gc_ctx_destroy(ctx: int) -> None:
+    load().gc_ctx_destroy(ctypes.c_void_p(ctx))
+
+
+def gc_color(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, round_cap: int = 0):
+    """Synchronous colouring; arrays may be host (numpy) or device (torch).
+    Returns (status, stats dict)."""
+    _check_i32(row_ptr, "row_ptr")
+    _check_i32(col_idx, "col_idx")
+    _check_i32(colors_out, "colors_out")
+    csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
+    st = gc_stats()
+    rs = None
+    if round_cap > 0:
+        rs = np.zeros(round_cap, np.int32)
+        st.round_sizes = rs.ctypes.data
+        st.round_sizes_cap = round_cap
+    rc = load().gc_color(ctypes.byref(csr), int(n), int(nnz), int(mode), _ptr(colors_out),
+                         ctypes.byref(st))
+    return rc, stats_dict(st, rs)
+
+
+def gc_color_async(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out,
+                   opts=None, stream=None) -> int:
+    """Enqueue one colouring (device arrays); returns the launch status."""
+    csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
+    o = _opts(opts)
+    return int(load().gc_color_async(ctypes.c_void_p(ctx), ctypes.byref(csr), int(n), int(nnz),
+                                     int(mode), ctypes.byref(o) if o is not None else None,
+                                     _ptr(colors_out), ctypes.c_void_p(_stream_handle(stream))))
+
+
+def gc_ctx_stats(ctx: int, round_cap: int = 0):
+    """Wait for the context's last colouring; returns (status, stats dict)."""
+    st = gc_stats()
+    rs = None
+    if round_cap > 0:
+        rs = np.zeros(round_cap, np.int32)
+        st.round_sizes = rs.ctypes.data
+        st.round_sizes_cap = round_cap
+    rc = load().gc_ctx_stats(ctypes.c_void_p(ctx), ctypes.byref(st))
+    return int(rc), stats_dict(st, rs)
+
+
+def gc_color_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, edge_off, row_ptr,
+                   col_idx, mode: int, colors_out, rounds_out=None, conflicts_out=None,
+                   opts=None, stream=None) -> int:
+    """Enqueue the colouring of a batch of graphs (device arrays)."""
+    b = gc_batch(int(G), int(total_n), int(total_nnz), _ptr(vtx_off), _ptr(edge_off),
+                 _ptr(row_ptr), _ptr(col_idx) if total_nnz else 0)
+    o = _opts(opts)
+    return int(load().gc_color_batch(ctypes.c_void_p(ctx), ctypes.byref(b), int(mode),
+                                     ctypes.byref(o) if o is not None else None,
+                                     _ptr(colors_out), _ptr(rounds_out), _ptr(conflicts_out),
+                                     ctypes.c_void_p(_stream_handle(stream))))
+
+
+class Context:
+    """Owns a gc_ctx; colours graphs held as torch CUDA tensors."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.handle = gc_ctx_create(device)
+
+    def close(self):
+        if self.handle:
+            gc_ctx_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def color(self, row_ptr, col_idx, mode: int = 0, colors_out=None, opts=None, stream=None,
+              round_cap: int = 0, check: bool = True):
+        """Colour one resident graph; returns (colors tensor, status, stats)."""
+        import torch
+        n = row_ptr.numel() - 1
+        if colors_out is None:
+            colors_out = torch.empty(max(n, 0), dtype=torch.int32, device=row_ptr.device)
+        rc = gc_color_async(self.handle, row_ptr, col_idx, n, col_idx.numel(), mode, colors_out,
+                            opts, stream)
+        if rc != GC_OK:
+            raise GCError(rc, "gc_color_async")
+        rc, st = gc_ctx_stats(self.handle, round_cap)
+        if check and rc not in (GC_OK,):
+            raise GCError(rc, "gc_ctx_stats")
+        return colors_out, rc, st
+
+    def color_batch(self, vtx_off, edge_off, row_ptr, col_idx, total_n: int, total_nnz: int,
+                    mode: int = 0, colors_out=None, per_graph: bool = True, opts=None,
+                    stream=None, check: bool = True):
+        """Colour every graph of a resident batch in one launch; returns
+        (colors, rounds[G], conflicts[G], status, stats)."""
+        import torch
+        G = vtx_off.numel() - 1
+        dev = row_ptr.device
+        if colors_out is None:
+            colors_out = torch.empty(max(total_n, 0), dtype=torch.int32, device=dev)
+        rounds = torch.empty(G, dtype=torch.int32, device=dev) if per_graph else None
+        confl = torch.empty(G, dtype=torch.int64, device=dev) if per_graph else None
+        rc = gc_color_batch(self.handle, G, total_n, total_nnz, vtx_off, edge_off, row_ptr,
+                            col_idx, mode, colors_out, rounds, confl, opts, stream)
+        if rc != GC_OK:
+            raise GCError(rc, "gc_color_batch")
+        rc, st = gc_ctx_stats(self.handle)
+        if check and rc != GC_OK:
+            raise GCError(rc, "gc_ctx_stats")
+        return colors_out, rounds, confl, rc, st
