@@ -75,10 +75,16 @@ enum {
                                     recolour (the Sec. 5 / Fig. 7 livelock);
                                     only meaningful with a small max_rounds */
     GC_NO_COLOR_STATS = 64,      /* skip the max/distinct colour reduction */
-    GC_REPAIR_SNAPSHOT = 128     /* with GC_SCHED_ASYNC and GC_ALG_RSOC: round 0
+    GC_REPAIR_SNAPSHOT = 128,    /* with GC_SCHED_ASYNC and GC_ALG_RSOC: round 0
                                     runs in place, every later round reads the
                                     colours of the end of the round before
                                     (fewer colours on dense cores, more rounds) */
+    GC_TIERS = 256               /* with GC_SCHED_ASYNC and GC_ALG_RSOC: colour
+                                    the vertices of degree > t2, then those of
+                                    degree > t1, then the rest, each tier taken
+                                    through round 0 and its repair rounds before
+                                    the next (later tiers are uncoloured while
+                                    an earlier one is repaired) */
 };
 
 /* ---- device error word bits (gc_stats.error_word) ---------------------- */

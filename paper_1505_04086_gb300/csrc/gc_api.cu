@@ -53,7 +53,7 @@ struct gc_ctx {
     int num_sms = 0;
     int occ[2][2] = {{0, 0}, {0, 0}};
     // scratch
-    Buf cB, wl0, wl1, hb0, hb1, hub_all, lut, bitmap, round_sizes, st, done;
+    Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done;
     Buf stage_rp, stage_ci, stage_col;  // gc_color host staging
     DevState *st_host = nullptr;        // pinned
     int32_t *rs_host = nullptr;         // pinned round sizes
@@ -117,6 +117,7 @@ int ensure_scratch(gc_ctx *c, int64_t n, bool need_b, bool batch, int64_t lut_en
     if (need_b && !c->cB.reserve(vb)) return GC_ERR_OOM;
     if (!c->wl0.reserve(vb) || !c->wl1.reserve(vb)) return GC_ERR_OOM;
     if (!c->hb0.reserve(vb) || !c->hb1.reserve(vb) || !c->hub_all.reserve(vb)) return GC_ERR_OOM;
+    if (!c->mid_all.reserve(vb)) return GC_ERR_OOM;
     if (batch && !c->lut.reserve((size_t)std::max<int64_t>(lut_entries, 1) * sizeof(int32_t))) return GC_ERR_OOM;
     if (!c->done.reserve(((size_t)std::max<int64_t>(n, 1) / 32 + 2) * sizeof(int32_t))) return GC_ERR_OOM;
     return GC_OK;
@@ -161,6 +162,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.hub[0] = c->hb0.as<int32_t>();
     p.hub[1] = c->hb1.as<int32_t>();
     p.hub_all = c->hub_all.as<int32_t>();
+    p.mid_all = c->mid_all.as<int32_t>();
     p.hub_cap = (int32_t)n;
 
     if ((e = cudaMemsetAsync(c->st.p, 0, sizeof(DevState), s)) != cudaSuccess) return cuda_status(e);
@@ -292,7 +294,7 @@ void gc_ctx_destroy(gc_ctx *c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     if (c->ev_done) cudaEventSynchronize(c->ev_done);
-    for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->lut, &c->bitmap,
+    for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
                    &c->round_sizes, &c->st, &c->done, &c->stage_rp, &c->stage_ci, &c->stage_col})
         b->release();
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -309,7 +311,7 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
                    int32_t *colors_out, void *stream)
 {
     if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
-    if (mode & ~(uint32_t)255) return GC_ERR_ARG;
+    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
     Resolved r;
@@ -443,7 +445,7 @@ int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o
                    int32_t *rounds_out, int64_t *conflicts_out, void *stream)
 {
     if (!c || !b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0) return GC_ERR_ARG;
-    if (mode & ~(uint32_t)255) return GC_ERR_ARG;
+    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
     if (b->G > 0 && (!b->vtx_off || !b->edge_off)) return GC_ERR_ARG;
     if (b->total_n > 0 && (!b->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (b->total_nnz > 0 && !b->col_idx) return GC_ERR_ARG;

@@ -32,6 +32,7 @@ struct DevState {
     int error;
     int rounds;
     int hub_all_count;
+    int mid_all_count;
     int max_color;
     unsigned long long conflicts;
     unsigned long long model_bytes;
@@ -63,6 +64,7 @@ struct KParams {
     int32_t *wl[2];
     int32_t *hub[2];
     int32_t *hub_all;
+    int32_t *mid_all;          // tiered mode: all vertices with t1 < deg <= t2
     int32_t hub_cap;
     DevState *st;
     int32_t *round_sizes;      // device, round_sizes_cap entries

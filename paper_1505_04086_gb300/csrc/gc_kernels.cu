@@ -284,6 +284,9 @@ __device__ int ff_warp(const KParams &p, int64_t beg, int deg, int32_t nbase, co
     return deg + 1;  // not reached: one of 1..deg+1 is always free
 }
 
+constexpr int kWarpUnroll = 4;   // entries per lane in flight (warp path)
+constexpr int kBlockUnroll = 4;  // entries per thread in flight (block path)
+
 template <bool ASYNC>
 __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
                             const int32_t *R, int cv, bool stop_early, int lane, int &t_total)
@@ -292,19 +295,29 @@ __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t en
     const int tie = p.tie;
     bool def = false;
     int t = 0;
-    for (int i0 = 0; i0 < deg; i0 += 32) {
-        const int ii = i0 + lane;
-        const bool in = ii < deg;
-        const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
-        const int32_t u = in ? nbase + __ldg(p.col_idx + k) : 0;
-        const bool side = in && on_tie_side(tie, u, v);
-        if (side) {
-            ++t;
-            if (ld_color<ASYNC>(R + u) == cv) def = true;
+    for (int i0 = 0; i0 < deg; i0 += 32 * kWarpUnroll) {
+        int32_t u[kWarpUnroll];
+        bool side[kWarpUnroll];
+#pragma unroll
+        for (int q = 0; q < kWarpUnroll; ++q) {
+            const int ii = i0 + q * 32 + lane;
+            const bool in = ii < deg;
+            const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
+            u[q] = in ? nbase + __ldg(p.col_idx + k) : 0;
+            side[q] = in && on_tie_side(tie, u[q], v);
         }
-        const unsigned sides = __ballot_sync(FULL_MASK, side);
+        int c[kWarpUnroll];
+#pragma unroll
+        for (int q = 0; q < kWarpUnroll; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < kWarpUnroll; ++q)
+            if (side[q]) {
+                ++t;
+                def |= (c[q] == cv);
+            }
+        const unsigned more = __ballot_sync(FULL_MASK, side[kWarpUnroll - 1]);
         const bool any_def = __any_sync(FULL_MASK, def);
-        if (tie != TIE_NONE && !(sides >> 31)) break;
+        if (tie != TIE_NONE && !(more >> 31)) break;
         if (any_def && stop_early) break;
     }
     t_total = __reduce_add_sync(FULL_MASK, t);
@@ -365,10 +378,18 @@ __device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, c
         for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) sh.hub_bm[w] = 0u;
         if (threadIdx.x == 0) sh.first = INT_MAX;
         __syncthreads();
-        for (int i = threadIdx.x; i < deg; i += kBlock) {
-            const int c = ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i));
-            const int d = c - base;
-            if (d >= 0 && d < kWin) atomicOr(&sh.hub_bm[d >> 5], 1u << (d & 31));
+        for (int i0 = 0; i0 < deg; i0 += kBlock * kBlockUnroll) {
+            int c[kBlockUnroll];
+#pragma unroll
+            for (int q = 0; q < kBlockUnroll; ++q) {
+                const int i = i0 + q * kBlock + threadIdx.x;
+                c[q] = (i < deg) ? ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i)) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < kBlockUnroll; ++q) {
+                const int d = c[q] - base;
+                if (c[q] >= 0 && d >= 0 && d < kWin) atomicOr(&sh.hub_bm[d >> 5], 1u << (d & 31));
+            }
         }
         __syncthreads();
         for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) {
@@ -394,17 +415,27 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
     int t = 0;
     if (threadIdx.x == 0) sh.tcount = 0;
     __syncthreads();
-    for (int i0 = 0; i0 < deg; i0 += kBlock) {
-        const int ii = i0 + threadIdx.x;
-        const bool in = ii < deg;
-        const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
-        const int32_t u = in ? nbase + __ldg(p.col_idx + k) : 0;
-        const bool side = in && on_tie_side(tie, u, v);
-        if (side) {
-            ++t;
-            if (ld_color<ASYNC>(R + u) == cv) def = true;
+    for (int i0 = 0; i0 < deg; i0 += kBlock * kBlockUnroll) {
+        int32_t u[kBlockUnroll];
+        bool side[kBlockUnroll];
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q) {
+            const int ii = i0 + q * kBlock + threadIdx.x;
+            const bool in = ii < deg;
+            const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
+            u[q] = in ? nbase + __ldg(p.col_idx + k) : 0;
+            side[q] = in && on_tie_side(tie, u[q], v);
         }
-        const int more = __syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side : 0);
+        int c[kBlockUnroll];
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q)
+            if (side[q]) {
+                ++t;
+                def |= (c[q] == cv);
+            }
+        const int more = __syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side[kBlockUnroll - 1] : 0);
         const int any_def = __syncthreads_or((int)def);
         if (tie != TIE_NONE && !more) break;
         if (any_def && stop_early) break;
@@ -460,7 +491,7 @@ __device__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, i
 // as outside; warp-path ids are coloured afterwards and see all lanes.
 template <bool BATCH>
 __device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C, long long &mb, uint32_t *bm,
-                                   int lane)
+                                   int lane, int dmax)
 {
     const long long vi = cbase + lane;
     int32_t v = vi < p.n ? (int32_t)vi : -1;
@@ -468,7 +499,7 @@ __device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C
     int32_t nbase = 0, g = 0;
     if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
     const int deg = (int)(end - beg);
-    const bool hub = v >= 0 && deg > p.t2;
+    const bool hub = v >= 0 && deg > dmax;  // coloured before this pass
     const bool mid = v >= 0 && !hub && deg > p.t1;
     const bool thr = v >= 0 && !hub && !mid;
     const unsigned hubmask = __ballot_sync(FULL_MASK, hub);
@@ -566,6 +597,7 @@ struct PassIn {
     int32_t n;                 // its length (or n for implicit)
     const int32_t *hub;        // hub worklist
     int32_t hn;
+    int32_t dmax;              // implicit passes skip vertices of higher degree
 };
 
 // Runs `op` over the hubs (block per vertex) and then the tiles (warp per
@@ -622,7 +654,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             if (base >= in.n) break;
             if (window > 0 && t >= window) wait_tile_done(p, t - window, lane);
             for (int j = 0; j < p.tile && base + j < in.n; j += 32)
-                chunk_tent_ordered<BATCH>(p, base + j, W, mb, sh.warp_bm[wid], lane);
+                chunk_tent_ordered<BATCH>(p, base + j, W, mb, sh.warp_bm[wid], lane, in.dmax);
             if (window > 0) publish_tile_done(p, t, lane);
         }
         return;
@@ -641,7 +673,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int32_t nbase = 0, g = 0;
             if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
             const int deg = (int)(end - beg);
-            if (in.implicit && deg > p.t2) v = -1;  // hubs went through the block phase
+            if (in.implicit && deg > in.dmax) v = -1;  // coloured in another phase / stage
             const bool mid = v >= 0 && deg > p.t1;
             bool d = false;
             if (v >= 0 && !mid) d = vertex_thread<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb);
@@ -695,6 +727,8 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
     // Snapshot rounds: deterministic mode, or asynchronous round 0 followed
     // by round-synchronous repair rounds (GC_REPAIR_SNAPSHOT, RSOC only).
     const bool snap = !twop && (!ASYNC || (p.mode & GC_REPAIR_SNAPSHOT) != 0);
+    // Degree tiers (asynchronous RSOC): hubs, then mid-degree, then the rest.
+    const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
     unsigned nbl = gridDim.x;
     long long mb = 0;
 
@@ -705,13 +739,14 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
         const long long stride = (long long)gridDim.x * kBlock;
         for (long long b0 = (long long)blockIdx.x * kBlock; b0 < p.n; b0 += stride) {
             const long long vi = b0 + threadIdx.x;
-            bool hub = false;
+            bool hub = false, midv = false;
             const int32_t v = (int32_t)vi;
             if (vi < p.n) {
                 int64_t beg, end;
                 int32_t nbase, g;
                 row_of<BATCH>(p, v, beg, end, nbase, g);
                 hub = (end - beg) > p.t2;
+                midv = tiers && !hub && (end - beg) > p.t1;
                 st_color<false>(p.cA + v, ASYNC ? 0 : 1);
                 if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
                 if (!ASYNC) mb += 4;
@@ -725,6 +760,18 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
                 if (hub) {
                     const int o = ob + __popc(m & ((1u << lane) - 1u));
                     if (o < p.hub_cap) __stcg(p.hub_all + o, v);
+                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+                }
+            }
+            const unsigned mm = __ballot_sync(FULL_MASK, midv);
+            if (mm) {
+                const int leader = __ffs(mm) - 1;
+                int ob = 0;
+                if (lane == leader) ob = atomicAdd(&st->mid_all_count, __popc(mm));
+                ob = __shfl_sync(FULL_MASK, ob, leader);
+                if (midv) {
+                    const int o = ob + __popc(mm & ((1u << lane) - 1u));
+                    if (o < p.n) __stcg(p.mid_all + o, v);
                     else atomicOr(&st->error, GC_EW_OVERFLOW);
                 }
             }
@@ -766,8 +813,8 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
 
         bool alive = ld_volatile(&st->error) == 0;
         const int hub_all_n = ld_volatile(&st->hub_all_count);
+        const int mid_all_n = ld_volatile(&st->mid_all_count);
         int q = 0;
-        PassIn in{true, nullptr, p.n, p.hub_all, hub_all_n};
         int window = p.window;
         if (ASYNC && window == 0) {
             // Ids of a naturally numbered mesh are local: neighbours would be
@@ -778,74 +825,102 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = window;
         }
 
-        // Asynchronous round 0 (Algorithm 3): tentative colouring of all of V.
-        if (alive && ASYNC && !twop) {
-            run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, 0, in, p.cA, p.cA, false, mb, window);
-            grid_sync(st, nbl);
-            alive = ld_volatile(&st->error) == 0;
+        // Stages: one (all of V), or, with tiers, hubs -> mid degree -> low
+        // degree, each taken through round 0 and its repair rounds before the
+        // next starts (vertices of later stages are still uncoloured then).
+        PassIn stages[3];
+        int nstages = 1;
+        if (tiers) {
+            stages[0] = PassIn{false, nullptr, 0, p.hub_all, hub_all_n, 0};
+            stages[1] = PassIn{false, p.mid_all, mid_all_n, nullptr, 0, 0};
+            stages[2] = PassIn{true, nullptr, p.n, nullptr, 0, p.t1};
+            nstages = 3;
+        } else {
+            stages[0] = PassIn{true, nullptr, p.n, p.hub_all, hub_all_n, p.t2};
         }
 
         int32_t *R = p.cA;
         int32_t *W = snap ? p.cB : p.cA;
         int32_t *last_written = p.cA;
         bool copy_back = false;
-        for (int it = 1; alive; ++it) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                st->wl_count[(it + 2) & (kRing - 1)] = 0;
-                st->hub_count[(it + 2) & (kRing - 1)] = 0;
-                st->wl_work[(it + 2) & (kRing - 1)] = 0;
-            }
-            if (twop) {
-                // Algorithm 2: phase 1 tentative colouring of U (in
-                // deterministic mode iteration 1's phase 1 is the fill of
-                // the prologue), barrier, phase 2 detection, barrier.
-                if (ASYNC || it > 1) {
-                    run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false, mb,
-                                           window);
-                    grid_sync(st, nbl);
-                    if (ld_volatile(&st->error)) break;
-                }
-                run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb);
-            } else {
-                // Algorithm 3: fused detect-and-recolour over U.
-                run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb);
-                last_written = W;
-            }
-            grid_sync(st, nbl);
-            if (ld_volatile(&st->error)) {
-                copy_back = true;
-                break;
-            }
-            const int nl = ld_volatile(&st->wl_count[it & (kRing - 1)]);
-            const int nh = ld_volatile(&st->hub_count[it & (kRing - 1)]);
-            const int tot = nl + nh;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                st->rounds = it;
-                st->conflicts += (unsigned long long)tot;
-                if (p.round_sizes && it - 1 < p.round_sizes_cap) p.round_sizes[it - 1] = tot;
-            }
-            if (snap) {
-                int32_t *t = R;
-                R = W;
-                W = t;
-            }
-            if (tot == 0) break;
-            if (it >= p.max_rounds) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->error, GC_EW_NO_CONVERGENCE);
-                copy_back = true;
-                break;
-            }
-            in = PassIn{false, p.wl[it & 1], nl, p.hub[it & 1], nh};
-            const unsigned long long work = *(volatile unsigned long long *)&st->wl_work[it & (kRing - 1)];
-            if (nbl > 1 && tot <= p.tail && work <= (unsigned long long)p.tail * kTailWorkPerVertex) {
-                // Few vertices left: block 0 finishes alone with block-local
-                // barriers; the others leave.
-                if (blockIdx.x != 0) {
+        int it = 0;
+        for (int sg = 0; sg < nstages && alive; ++sg) {
+            PassIn in = stages[sg];
+            if (in.n == 0 && in.hn == 0) continue;
+            const bool last_stage = sg == nstages - 1;
+            // Asynchronous round 0 (Algorithm 3): tentative colouring of the
+            // stage's vertices, in place on the current colours.
+            if (ASYNC && !twop) {
+                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, 0, in, R, R, false, mb, window);
+                grid_sync(st, nbl);
+                if (ld_volatile(&st->error)) {
                     alive = false;
                     break;
                 }
-                nbl = 1;
             }
+            for (;;) {
+                ++it;
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    st->wl_count[(it + 2) & (kRing - 1)] = 0;
+                    st->hub_count[(it + 2) & (kRing - 1)] = 0;
+                    st->wl_work[(it + 2) & (kRing - 1)] = 0;
+                }
+                if (twop) {
+                    // Algorithm 2: phase 1 tentative colouring of U (in
+                    // deterministic mode iteration 1's phase 1 is the fill of
+                    // the prologue), barrier, phase 2 detection, barrier.
+                    if (ASYNC || it > 1) {
+                        run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false,
+                                               mb, window);
+                        grid_sync(st, nbl);
+                        if (ld_volatile(&st->error)) {
+                            alive = false;
+                            break;
+                        }
+                    }
+                    run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb);
+                } else {
+                    // Algorithm 3: fused detect-and-recolour over U.
+                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb);
+                    last_written = W;
+                }
+                grid_sync(st, nbl);
+                if (ld_volatile(&st->error)) {
+                    copy_back = true;
+                    break;
+                }
+                const int nl = ld_volatile(&st->wl_count[it & (kRing - 1)]);
+                const int nh = ld_volatile(&st->hub_count[it & (kRing - 1)]);
+                const int tot = nl + nh;
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    st->rounds = it;
+                    st->conflicts += (unsigned long long)tot;
+                    if (p.round_sizes && it - 1 < p.round_sizes_cap) p.round_sizes[it - 1] = tot;
+                }
+                if (snap) {
+                    int32_t *t = R;
+                    R = W;
+                    W = t;
+                }
+                if (tot == 0) break;
+                if (it >= p.max_rounds) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&st->error, GC_EW_NO_CONVERGENCE);
+                    copy_back = true;
+                    break;
+                }
+                in = PassIn{false, p.wl[it & 1], nl, p.hub[it & 1], nh, p.t2};
+                const unsigned long long work = *(volatile unsigned long long *)&st->wl_work[it & (kRing - 1)];
+                if (last_stage && nbl > 1 && tot <= p.tail && work <= (unsigned long long)p.tail * kTailWorkPerVertex) {
+                    // Few vertices left: block 0 finishes alone with block-local
+                    // barriers; the others leave.
+                    if (blockIdx.x != 0) {
+                        alive = false;
+                        break;
+                    }
+                    nbl = 1;
+                }
+            }
+            if (copy_back) break;
         }
         // Deterministic RSOC stopped early (cap or error): the latest colours
         // may sit in the second buffer.  On normal termination both buffers

@@ -43,6 +43,7 @@ GC_CHECKED = 16
 GC_DEBUG_NO_TIEBREAK = 32
 GC_NO_COLOR_STATS = 64
 GC_REPAIR_SNAPSHOT = 128
+GC_TIERS = 256
 
 # error word bits
 GC_EW_TIMEOUT = 1
