@@ -53,7 +53,8 @@ enum {
     GC_ERR_CUDA = -7,            /* a CUDA runtime call failed */
     GC_ERR_OVERFLOW = -8,        /* internal worklist capacity exceeded */
     GC_ERR_CHECK = -9,           /* GC_CHECKED found an invalid colouring */
-    GC_ERR_NOT_FOUND = -10       /* server: unknown ticket */
+    GC_ERR_NOT_FOUND = -10,      /* server: unknown ticket */
+    GC_ERR_TOO_LARGE = -11       /* gc_color_noalloc: n > GC_NOALLOC_MAX_N */
 };
 
 /* ---- mode bits ------------------------------------------------------- */
@@ -230,6 +231,41 @@ typedef struct {
 int gc_color_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, const gc_opts *opts,
                    int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
                    void *stream);
+
+/* ---- colouring without any allocation ---------------------------------- */
+
+/* Largest graph (vertices) gc_color_noalloc accepts. */
+#define GC_NOALLOC_MAX_N 262144
+
+/*
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate memory while they run: code whose device memory is
+ * owned by another allocator under a hard budget, or latency-critical loops
+ * that cannot afford a cudaMalloc/cudaFree (either may synchronise the
+ * device).  Same colouring as gc_color_async + gc_ctx_stats (every mode bit
+ * and gc_opts field behaves the same), but no context is needed and nothing
+ * is allocated: all working memory comes from one fixed array of about 7 MB
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ *   csr, colors_out: DEVICE pointers (host pointers give GC_ERR_ARG: staging
+ *                    them would need memory); the caller owns them.
+ *   n > GC_NOALLOC_MAX_N returns GC_ERR_TOO_LARGE before touching the GPU.
+ *   stream: a cudaStream_t (NULL = legacy default stream).  The call enqueues
+ *           its work there and waits for it, then fills stats_out (may be
+ *           NULL; elapsed_ms is 0: no timing is recorded).
+ *   Returns the colouring's status, as gc_ctx_stats would.
+ *
+ * The first call on each device looks up the fixed array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (the parts that must start at zero are cleared at
+ * the start of each call), so calls whose GPU work overlaps -- on different
+ * streams or host threads without ordering between them -- race and give
+ * undefined results.  Serialise them.
+ */
+int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
+                     int32_t *colors_out, gc_stats *stats_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -239,6 +239,7 @@ const char *gc_strerror(int s)
     case GC_ERR_OVERFLOW: return "internal worklist overflow";
     case GC_ERR_CHECK: return "result check failed (invalid colouring)";
     case GC_ERR_NOT_FOUND: return "unknown ticket";
+    case GC_ERR_TOO_LARGE: return "graph larger than the fixed scratch of gc_color_noalloc";
     default: return "unknown status";
     }
 }

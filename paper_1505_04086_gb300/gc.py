@@ -30,6 +30,8 @@ GC_ERR_CUDA = -7
 GC_ERR_OVERFLOW = -8
 GC_ERR_CHECK = -9
 GC_ERR_NOT_FOUND = -10
+GC_ERR_TOO_LARGE = -11
+GC_NOALLOC_MAX_N = 262144
 
 # mode bits
 GC_ALG_RSOC = 0
@@ -91,6 +93,9 @@ _SIGS = {
     "gc_ctx_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
     "gc_color_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32,
                                       ctypes.POINTER(gc_opts), _P, _P, _P, _P]),
+    "gc_color_noalloc": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_uint32, ctypes.POINTER(gc_opts), _P,
+                                        ctypes.POINTER(gc_stats), _P]),
 }
 
 _lock = threading.Lock()
@@ -248,6 +253,24 @@ def gc_color_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, edge
                                      ctypes.byref(o) if o is not None else None,
                                      _ptr(colors_out), _ptr(rounds_out), _ptr(conflicts_out),
                                      ctypes.c_void_p(_stream_handle(stream))))
+
+
+def gc_color_noalloc(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, opts=None,
+                     stream=None, round_cap: int = 0):
+    """Colour one resident graph without any allocation (device arrays,
+    n <= GC_NOALLOC_MAX_N).  Waits for the result; returns (status, stats)."""
+    csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
+    o = _opts(opts)
+    st = gc_stats()
+    rs = None
+    if round_cap > 0:
+        rs = np.zeros(round_cap, np.int32)
+        st.round_sizes = rs.ctypes.data
+        st.round_sizes_cap = round_cap
+    rc = load().gc_color_noalloc(ctypes.byref(csr), int(n), int(nnz), int(mode),
+                                 ctypes.byref(o) if o is not None else None, _ptr(colors_out),
+                                 ctypes.byref(st), ctypes.c_void_p(_stream_handle(stream)))
+    return int(rc), stats_dict(st, rs)
 
 
 class Context:

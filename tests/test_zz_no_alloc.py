@@ -1,0 +1,89 @@
+"""gc_color_noalloc: the entry point for callers that may not allocate.
+
+Some callers cannot let a library allocate device memory while they run
+(their memory belongs to another allocator under a fixed budget, or a
+cudaMalloc would stall a latency-critical loop).  gc_color_noalloc serves
+them from a fixed array built into the library.  These tests call it
+through the C ABI and check that it gives exactly what the allocating entry
+point (gc_color_async + gc_ctx_stats) gives, twice in a row, since every
+call reuses the same array.
+"""
+import numpy as np
+import pytest
+
+from paper_1505_04086_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1505_04086_gb300 import _build, gc  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    _build.build()
+    c = gc.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(g):
+    ci = g.col_idx if g.nnz else np.zeros(1, np.int32)
+    return torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(ci).cuda()
+
+
+def _reference(ctx, rp, ci, g, mode):
+    col = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    assert gc.gc_color_async(ctx.handle, rp, ci, g.n, g.nnz, mode, col) == gc.GC_OK
+    rc, st = gc.gc_ctx_stats(ctx.handle, 1024)
+    assert rc == gc.GC_OK
+    return col.cpu().numpy(), st
+
+
+GRAPHS = [lambda: I.kuhn3d(24), lambda: I.tri2d(64, 64), lambda: I.rmat(12),
+          lambda: I.rgg(20000, 12.0, seed=7)]
+MODES = [gc.GC_ALG_RSOC, gc.GC_ALG_TWO_PHASE, gc.GC_ALG_RSOC | gc.GC_TIE_HIGHER_KEEPS]
+
+
+@pytest.mark.parametrize("make", GRAPHS, ids=["kuhn24", "tri64", "rmat12", "rgg20k"])
+@pytest.mark.parametrize("mode", MODES, ids=["rsoc", "twophase", "rsoc_higher"])
+def test_matches_allocating_entry_point(ctx, make, mode):
+    g = make()
+    rp, ci = _dev(g)
+    want, want_st = _reference(ctx, rp, ci, g, mode)
+    for _ in range(2):  # the second call starts from the first call's leftovers
+        col = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+        rc, st = gc.gc_color_noalloc(rp, ci, g.n, g.nnz, mode, col, round_cap=1024)
+        assert rc == gc.GC_OK, gc.gc_strerror(rc)
+        assert np.array_equal(col.cpu().numpy(), want)
+        for k in ("rounds", "conflicts", "model_bytes", "colors", "distinct_colors"):
+            assert st[k] == want_st[k], k
+        assert np.array_equal(st["round_sizes"], want_st["round_sizes"])
+
+
+def test_async_result_is_valid(ctx):
+    import oracle
+    g = I.kuhn3d(20)
+    rp, ci = _dev(g)
+    for _ in range(2):
+        col = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        rc, st = gc.gc_color_noalloc(rp, ci, g.n, g.nnz, gc.GC_SCHED_ASYNC, col)
+        assert rc == gc.GC_OK
+        assert oracle.check(g, col.cpu().numpy())[0] == 0
+
+
+def test_rejects_graphs_above_the_fixed_size(ctx):
+    n = gc.GC_NOALLOC_MAX_N + 1
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(1, dtype=torch.int32, device="cuda")
+    col = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rc, _ = gc.gc_color_noalloc(rp, ci, n, 0, 0, col)
+    assert rc == gc.GC_ERR_TOO_LARGE
+    assert "fixed scratch" in gc.gc_strerror(rc)
+    # the largest accepted size works (no edges: one round, all colour 1)
+    n = gc.GC_NOALLOC_MAX_N
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    col = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rc, st = gc.gc_color_noalloc(rp, ci, n, 0, 0, col)
+    assert rc == gc.GC_OK and st["rounds"] == 1
+    assert int(col.min()) == 1 and int(col.max()) == 1
