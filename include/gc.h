@@ -124,6 +124,12 @@ typedef struct {
     int32_t *round_sizes;        /* optional caller-owned HOST array; receives
                                     |L| of each iteration */
     int32_t round_sizes_cap;     /* its capacity (entries) */
+    int64_t *round_ns;           /* optional caller-owned HOST array: [0] = ns
+                                    from kernel start to the end of round 0
+                                    (the prologue for deterministic runs),
+                                    [k] = to the end of iteration k (device
+                                    clock; first 255 iterations) */
+    int32_t round_ns_cap;        /* its capacity (entries) */
 } gc_stats;
 
 /* Tuning knobs; zero-initialise for defaults. */

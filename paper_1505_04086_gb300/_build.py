@@ -44,16 +44,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libgc.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, defines=None, out: str | None = None,
+          build_dir: str | None = None) -> str:
+    """Compile (if needed) and return the path of libgc.so.  `defines`
+    (e.g. {"GC_THREAD_UNROLL": 16}), `out` and `build_dir` build a variant
+    library elsewhere (tuning experiments); the defaults build the product."""
+    lib = out or LIB
+    bdir = build_dir or BUILD
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I", INCLUDE, "-I", CSRC]
+    for k, v in (defines or {}).items():
+        common.append(f"-D{k}={v}")
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
             cmd = [nvcc] + common + ["-c", s, "-o", o + ".tmp"]
@@ -68,15 +75,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             os.replace(o + ".tmp", o)
     if failed:
         raise RuntimeError("nvcc failed while building libgc")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
             "-Xlinker", f"-rpath,{_cuda_lib_dir()}"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -391,6 +391,14 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
         }
         s.round_sizes = rs;
         s.round_sizes_cap = cap;
+        s.round_ns = out->round_ns;
+        s.round_ns_cap = out->round_ns_cap;
+        if (s.round_ns && s.round_ns_cap > 0) {
+            const DevState &d = *c->st_host;
+            const int k = std::min<int>(std::min<int>(s.rounds + 1, s.round_ns_cap), gc::kStamps);
+            for (int i = 0; i < k; ++i)
+                s.round_ns[i] = (c->last_empty || d.stamp[i] == 0) ? 0 : (int64_t)(d.stamp[i] - d.t_start);
+        }
         *out = s;
     }
     return status;
@@ -499,3 +507,14 @@ int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o
 }
 
 }  // extern "C"
+
+#ifdef GC_PHASE_TIMING
+// Tuning builds only: the phase cycle counters of the context's last call.
+extern "C" int gc_debug_phase_cycles(gc_ctx *c, unsigned long long *out16)
+{
+    if (!c || !out16) return GC_ERR_ARG;
+    if (cudaEventSynchronize(c->ev_done) != cudaSuccess) return GC_ERR_CUDA;
+    memcpy(out16, c->st_host->dbg, sizeof(c->st_host->dbg));
+    return GC_OK;
+}
+#endif

@@ -15,9 +15,14 @@ constexpr int kT1Max = 62;              // thread path keeps colours in a 64-bit
 constexpr int kT2Max = 4096;            // warp path bitmap covers colours 0..kT2Max+1
 constexpr int kWarpBmWords = (kT2Max + 2) / 32 + 1;
 constexpr int kHubBmWords = 256;        // block path: 8192-colour window per pass
+#ifndef GC_SEG_CAP
+#define GC_SEG_CAP 512
+#endif
+constexpr int kSegCap = GC_SEG_CAP;     // staged adjacency entries per buffer (2 per warp)
 constexpr int kLutShift = 10;           // batch: graph lookup per 1024 vertices
 constexpr int kRing = 4;                // round-counter ring depth
 constexpr int kStatBitmapWords = 1 << 15;  // distinct-colour bitmap: colours < 2^20
+constexpr int kStamps = 256;            // per-iteration end times kept in DevState
 constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
@@ -42,9 +47,12 @@ struct DevState {
     int hub_count[kRing];      // per-iteration push counters (hub list)
     unsigned long long wl_work[kRing];  // per-iteration sum of degrees pushed
     int distinct;
+    unsigned long long dbg[16];      // phase cycle counters (builds with GC_PHASE_TIMING only)
     int window;                // round-0 in-flight window in tiles (-1: unlimited)
     unsigned long long near_lower;   // locality sample: lower neighbours within kNearIds
     unsigned long long all_lower;    // locality sample: all lower neighbours
+    unsigned long long t_start;      // globaltimer at kernel start (ns)
+    unsigned long long stamp[kStamps];  // [0]: end of round 0, [k]: end of iteration k
 };
 
 struct KParams {

@@ -25,6 +25,19 @@ namespace gc {
 
 #define FULL_MASK 0xffffffffu
 
+// Phase cycle accounting for tuning builds (-DGC_PHASE_TIMING): lane 0 of a
+// warp adds the clock64 cycles of a phase to DevState::dbg[slot].
+#ifdef GC_PHASE_TIMING
+#define PT_BEGIN(var) long long var = clock64()
+#define PT_END(st, slot, var)                                                          \
+    do {                                                                                \
+        if ((threadIdx.x & 31) == 0) atomicAdd(&(st)->dbg[slot], (unsigned long long)(clock64() - (var))); \
+    } while (0)
+#else
+#define PT_BEGIN(var)
+#define PT_END(st, slot, var)
+#endif
+
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
 constexpr unsigned kBarrierMaxPolls = 1u << 26;
 
@@ -52,6 +65,52 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 }
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+// mbarrier + 1-D bulk (TMA) copy helpers for staging adjacency segments.
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr)
+{
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred done;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 done, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, done;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of
+// 16; completion is signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
 // Colour loads/stores.  Asynchronous mode reads colours that other threads
 // are writing in the same round: relaxed gpu-scope accesses, which are
@@ -87,6 +146,7 @@ __device__ __forceinline__ void st_color(int32_t *p, int v)
 // caller checks the error word after every barrier.
 __device__ void grid_sync(DevState *st, unsigned nblocks)
 {
+    PT_BEGIN(t_bar);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -112,6 +172,7 @@ __device__ void grid_sync(DevState *st, unsigned nblocks)
         }
     }
     __syncthreads();
+    PT_END(st, 8, t_bar);
 }
 
 // ------------------------------------------------------------------------
@@ -152,19 +213,36 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 // thread per vertex (deg <= t1 <= 62)
 // ------------------------------------------------------------------------
 
-constexpr int kUnroll = 8;
+#ifndef GC_THREAD_UNROLL
+#define GC_THREAD_UNROLL 8
+#endif
+#ifndef GC_MIN_BLOCKS
+#define GC_MIN_BLOCKS 4
+#endif
+constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
+
+// Adjacency entry k (a global CSR index) of the row being processed: read
+// from col_idx, or from the warp's staged copy of the chunk's segment.
+struct GlobalEnts {
+    const int32_t *col;
+    __device__ __forceinline__ int32_t operator()(int64_t k) const { return __ldg(col + k); }
+};
+struct StagedEnts {
+    const int32_t *buf;        // shared memory: entry k is buf[k - off]
+    int64_t off;
+    __device__ __forceinline__ int32_t operator()(int64_t k) const { return buf[k - off]; }
+};
 
 // Smallest colour >= 1 not held by any neighbour (Algorithm 1 body).  With
 // deg <= 62 the answer is <= 63, so a 64-bit mask of colours 1..64 suffices.
-template <bool ASYNC>
-__device__ __forceinline__ int ff_thread(const KParams &p, int64_t beg, int deg, int32_t nbase,
-                                         const int32_t *R)
+template <bool ASYNC, class E>
+__device__ __forceinline__ int ff_thread(const E &ent, int64_t beg, int deg, int32_t nbase, const int32_t *R)
 {
     unsigned long long mask = 0;
     for (int i = 0; i < deg; i += kUnroll) {
         int u[kUnroll];
 #pragma unroll
-        for (int q = 0; q < kUnroll; ++q) u[q] = (i + q < deg) ? nbase + __ldg(p.col_idx + beg + i + q) : -1;
+        for (int q = 0; q < kUnroll; ++q) u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
         int c[kUnroll];
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) c[q] = (u[q] >= 0) ? ld_color<ASYNC>(R + u[q]) : 0;
@@ -179,13 +257,11 @@ __device__ __forceinline__ int ff_thread(const KParams &p, int64_t beg, int deg,
 
 // Is some neighbour on v's tie side coloured cv?  t = tie-side entries seen
 // (the whole tie side unless stop_early ended the scan at a conflict).
-template <bool ASYNC>
-__device__ __forceinline__ bool detect_thread(const KParams &p, int32_t v, int64_t beg, int64_t end,
-                                              int32_t nbase, const int32_t *R, int cv,
-                                              bool stop_early, int &t)
+template <bool ASYNC, class E>
+__device__ __forceinline__ bool detect_thread(const E &ent, int tie, int32_t v, int64_t beg, int64_t end,
+                                              int32_t nbase, const int32_t *R, int cv, bool stop_early, int &t)
 {
     const int deg = (int)(end - beg);
-    const int tie = p.tie;
     bool def = false;
     t = 0;
     for (int i = 0; i < deg; i += kUnroll) {
@@ -196,7 +272,7 @@ __device__ __forceinline__ bool detect_thread(const KParams &p, int32_t v, int64
             const int ii = i + q;
             const bool in = ii < deg;
             const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
-            u[q] = in ? nbase + __ldg(p.col_idx + k) : 0;
+            u[q] = in ? nbase + ent(k) : 0;
             side[q] = in && on_tie_side(tie, u[q], v);
         }
         int c[kUnroll];
@@ -216,29 +292,29 @@ __device__ __forceinline__ bool detect_thread(const KParams &p, int32_t v, int64
 
 // One vertex, one thread.  Returns true if v must join the next worklist.
 // Byte model accounting goes to mb (see gc.h, gc_stats.model_bytes).
-template <bool ASYNC>
-__device__ __forceinline__ bool vertex_thread(const KParams &p, int op, int32_t v, int64_t beg, int64_t end,
-                                              int32_t nbase, const int32_t *R, int32_t *W, bool implicit,
-                                              long long &mb)
+template <bool ASYNC, class E>
+__device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, int op, int32_t v, int64_t beg,
+                                              int64_t end, int32_t nbase, const int32_t *R, int32_t *W,
+                                              bool implicit, long long &mb)
 {
     const int deg = (int)(end - beg);
     mb += (implicit ? 0 : 4) + 8;
     if (op == OP_TENT) {
-        st_color<ASYNC>(W + v, ff_thread<ASYNC>(p, beg, deg, nbase, R));
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R));
         mb += 8ll * deg + 4;
         return false;
     }
     const int cv = ld_color<ASYNC>(R + v);
     mb += 4;
     int t;
-    const bool d = detect_thread<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, t);
+    const bool d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t);
     if (op == OP_DETECT) {
         if (!ASYNC) st_color<false>(p.cA + v, cv);  // two-phase: bring buffer A up to date
         mb += 8ll * t + (d ? 4 : 0);
         return d;
     }
     if (d) {
-        st_color<ASYNC>(W + v, ff_thread<ASYNC>(p, beg, deg, nbase, R));
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R));
         mb += 8ll * deg + 8;
     } else {
         if (W != R) st_color<ASYNC>(W + v, cv);  // snapshot rounds: carry the colour over
@@ -362,6 +438,8 @@ __device__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, in
 // ------------------------------------------------------------------------
 
 struct Shared {
+    int32_t seg[kWarps][2][kSegCap];         // staged adjacency segments (double buffer per warp)
+    unsigned long long mbar[kWarps][2];      // their completion barriers
     uint32_t warp_bm[kWarps][kWarpBmWords];
     uint32_t hub_bm[kHubBmWords];
     int first;
@@ -489,16 +567,16 @@ __device__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, i
 // every neighbour outside the chunk.  This removes the lock-step tie of
 // Sec. 5 / Fig. 7 inside a warp.  Hub ids (coloured before the tiles) count
 // as outside; warp-path ids are coloured afterwards and see all lanes.
-template <bool BATCH>
-__device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C, long long &mb, uint32_t *bm,
-                                   int lane, int dmax)
+// Returns true on lanes whose vertex may end round 0 in conflict with a
+// neighbour it can lose to (see `suspect` below); such vertices form the
+// first repair worklist instead of all of V.
+template <class E>
+__device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cbase, int32_t v, int64_t beg,
+                                   int64_t end, int32_t nbase, int32_t *C, long long &mb, uint32_t *bm, int lane,
+                                   int dmax)
 {
-    const long long vi = cbase + lane;
-    int32_t v = vi < p.n ? (int32_t)vi : -1;
-    int64_t beg = 0, end = 0;
-    int32_t nbase = 0, g = 0;
-    if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
     const int deg = (int)(end - beg);
+    const int tie = p.tie;
     const bool hub = v >= 0 && deg > dmax;  // coloured before this pass
     const bool mid = v >= 0 && !hub && deg > p.t1;
     const bool thr = v >= 0 && !hub && !mid;
@@ -506,13 +584,22 @@ __device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C
     const unsigned midmask = __ballot_sync(FULL_MASK, mid);
     unsigned long long ext = 0;
     unsigned low = 0;
+    // Every vertex is written once in round 0, so a non-zero colour read
+    // for a neighbour is that neighbour's final round-0 colour and the
+    // First-Fit choice avoids it.  Lanes inside the chunk are resolved in
+    // id order (a higher or warp-path lane sees this lane's final colour).
+    // So an edge can end round 0 monochromatic only if one endpoint read the
+    // other as uncoloured: that endpoint is the suspect when the tie-break
+    // makes it the one to recolour.
+    bool suspect = mid;
+    PT_BEGIN(t_g);
     if (thr) {
         for (int i = 0; i < deg; i += kUnroll) {
             int u[kUnroll];
             bool outside[kUnroll];
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
-                u[q] = (i + q < deg) ? nbase + __ldg(p.col_idx + beg + i + q) : -1;
+                u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
                 const long long d = (long long)u[q] - cbase;
                 const bool inside = u[q] >= 0 && d >= 0 && d < 32 && !((hubmask >> d) & 1u);
                 if (inside && u[q] < v && !((midmask >> d) & 1u)) low |= 1u << d;
@@ -525,15 +612,29 @@ __device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C
             for (int q = 0; q < kUnroll; ++q) {
                 const unsigned b = (unsigned)(c[q] - 1);
                 if (b < 64u) ext |= 1ull << b;
+                if (outside[q] && c[q] == 0 && on_tie_side(tie, u[q], v)) suspect = true;
             }
         }
     }
-    int mine = 0;
-    for (int k = 0; k < 32; ++k) {
-        if (lane == k && thr) mine = __ffsll((long long)~ext);
-        const int ck = __shfl_sync(FULL_MASK, mine, k);
-        if ((low >> k) & 1u) ext |= 1ull << (ck - 1);
+    __syncwarp();
+    PT_END(p.st, 6, t_g);
+    PT_BEGIN(t_r);
+    int mine = thr ? __ffsll((long long)~ext) : 0;
+    // In-chunk dependencies: walk only the lanes between the first lane some
+    // lane depends on and the last dependent lane, in id order.
+    const unsigned dependent = __ballot_sync(FULL_MASK, low != 0u);
+    if (dependent) {
+        const unsigned needed = __reduce_or_sync(FULL_MASK, low);
+        const int k0 = __ffs(needed) - 1;
+        const int k1 = 31 - __clz(dependent);
+        for (int k = k0; k <= k1; ++k) {
+            if (lane == k && thr) mine = __ffsll((long long)~ext);
+            const int ck = __shfl_sync(FULL_MASK, mine, k);
+            if ((low >> k) & 1u) ext |= 1ull << (ck - 1);
+        }
+        if (thr && lane > k1) mine = __ffsll((long long)~ext);
     }
+    PT_END(p.st, 7, t_r);
     if (thr) {
         st_color<true>(C + v, mine);
         mb += 8 + 8ll * deg + 4;
@@ -549,6 +650,7 @@ __device__ void chunk_tent_ordered(const KParams &p, long long cbase, int32_t *C
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
         vertex_warp<true>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane);
     }
+    return suspect;
 }
 
 // Wait (bounded) until tile t of the ordered pass has been published.
@@ -600,12 +702,217 @@ struct PassIn {
     int32_t dmax;              // implicit passes skip vertices of higher degree
 };
 
+// Warp-aggregated append of the lanes with d set to the tile worklist of
+// iteration `it` (one atomic per warp); their degrees feed the tail test.
+// `stats`: count them as conflicts of their graph (batch statistics).
+template <bool BATCH>
+__device__ __forceinline__ void push_lanes(const KParams &p, bool d, int32_t v, int deg, int32_t g, int it,
+                                           int lane, bool stats)
+{
+    DevState *st = p.st;
+    const unsigned m = __ballot_sync(FULL_MASK, d);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    unsigned long long work = d ? (unsigned long long)deg : 0ull;
+    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(FULL_MASK, work, o);
+    int ob = 0;
+    if (lane == leader) {
+        ob = atomicAdd(&st->wl_count[it & (kRing - 1)], __popc(m));
+        atomicAdd(&st->wl_work[it & (kRing - 1)], work);
+    }
+    ob = __shfl_sync(FULL_MASK, ob, leader);
+    if (d) {
+        const int o = ob + __popc(m & ((1u << lane) - 1u));
+        if (o < p.n) __stcg(p.wl[it & 1] + o, v);
+        else atomicOr(&st->error, GC_EW_OVERFLOW);
+        if (stats) note_push_graph<BATCH>(p, g, it);
+    }
+}
+
+// One chunk of up to 32 worklist entries, one per lane (v = -1: none):
+// thread-path lanes run `op` with adjacency entries from `ent`, the warp
+// takes the mid-degree lanes one by one, and defective vertices are
+// appended to the worklist of iteration `it` (warp-aggregated).
+template <bool ASYNC, bool BATCH, class E>
+__device__ __forceinline__ void chunk_ops(const KParams &p, Shared &sh, const E &ent, int op, int it,
+                                          bool implicit, int dmax, int32_t v, int64_t beg, int64_t end,
+                                          int32_t nbase, int32_t g, const int32_t *R, int32_t *W, bool push,
+                                          long long &mb, int lane, int wid)
+{
+    const int deg = (int)(end - beg);
+    if (implicit && deg > dmax) v = -1;  // coloured in another phase / stage
+    const bool mid = v >= 0 && deg > p.t1;
+    bool d = false;
+    if (v >= 0 && !mid) d = vertex_thread<ASYNC>(p, ent, op, v, beg, end, nbase, R, W, implicit, mb);
+    unsigned mm = __ballot_sync(FULL_MASK, mid);
+    while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const int32_t vv = __shfl_sync(FULL_MASK, v, src);
+        const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
+        const int64_t ee = __shfl_sync(FULL_MASK, end, src);
+        const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
+        const bool dd = vertex_warp<ASYNC>(p, op, vv, bb, ee, nb, R, W, implicit, mb, sh.warp_bm[wid], lane);
+        if (lane == src) d = dd;
+    }
+    if (push) push_lanes<BATCH>(p, d, v, deg, g, it, lane, true);
+}
+
+// A chunk of 32 consecutive ids in a pass over V, with its rows and (when
+// its adjacency segment fits a buffer) a bulk copy of that segment in flight.
+struct Chunk {
+    long long cb;              // first id; -1: no chunk
+    int tile, kin;             // claimed tile and chunk index inside it
+    int32_t v, nbase, g;       // lane's vertex (-1: none) and graph
+    int64_t beg, end;          // lane's row
+    int64_t soff;              // entry index held by seg[slot][0]; -1: not staged
+};
+
+constexpr unsigned kStagePolls = 1u << 22;
+
+// Load the lanes' row pointers of chunk c and start the 1-D TMA copy of the
+// chunk's contiguous adjacency segment into seg[wid][slot].  The copy runs
+// 16-byte aligned; a segment that does not fit, or whose aligned end would
+// pass the last full 16 bytes of col_idx, is read from global memory instead.
+template <bool BATCH>
+__device__ __forceinline__ void stage_chunk(const KParams &p, Shared &sh, Chunk &c, long long n, int slot,
+                                            int lane, int wid, long long lim16)
+{
+    c.v = -1;
+    c.beg = c.end = 0;
+    c.nbase = 0;
+    c.g = 0;
+    c.soff = -1;
+    if (c.cb < 0) return;
+    const long long vi = c.cb + lane;
+    if (vi < n) {
+        c.v = (int32_t)vi;
+        row_of<BATCH>(p, c.v, c.beg, c.end, c.nbase, c.g);
+    }
+    const int last = (int)min(31ll, n - 1 - c.cb);
+    const long long s0 = __shfl_sync(FULL_MASK, (long long)c.beg, 0);
+    const long long e0 = __shfl_sync(FULL_MASK, (long long)c.end, last);
+    const long long a0 = (s0 * 4) & ~15ll;
+    const long long a1 = (e0 * 4 + 15) & ~15ll;
+    if (e0 > s0 && a1 - a0 <= (long long)kSegCap * 4 && a1 <= lim16) {
+        c.soff = a0 >> 2;
+        if (lane == 0) {
+            fence_proxy_async_smem();  // earlier reads of this buffer precede the copy
+            mbar_arrive_expect_tx(&sh.mbar[wid][slot], (uint32_t)(a1 - a0));
+            bulk_copy_g2s(sh.seg[wid][slot], reinterpret_cast<const char *>(p.col_idx) + a0, (uint32_t)(a1 - a0),
+                          &sh.mbar[wid][slot]);
+        }
+    }
+}
+
+// Bounded wait for the copy into seg[wid][slot]; on timeout the error word
+// gets GC_EW_TIMEOUT and the copy is waited for once more (bounded) so that
+// it does not land after the block has moved on.
+__device__ __forceinline__ bool wait_stage(const KParams &p, Shared &sh, int slot, uint32_t &phase, int wid)
+{
+    const uint32_t par = (phase >> slot) & 1u;
+    phase ^= 1u << slot;
+    unsigned polls = 0;
+    while (!mbar_try_wait(&sh.mbar[wid][slot], par)) {
+        if (++polls > kStagePolls) {
+            atomicOr(&p.st->error, GC_EW_TIMEOUT);
+            for (unsigned k = 0; k < kStagePolls && !mbar_try_wait(&sh.mbar[wid][slot], par); ++k) {
+            }
+            return false;
+        }
+    }
+    return true;
+}
+
+// Pass over all of V (implicit worklist): each warp walks the chunks of the
+// tiles it claims in id order, staging chunk j+1 while it works on chunk j.
+// The asynchronous tentative pass resolves lanes in id order and keeps at
+// most `window` tiles in flight (window <= 0: no limit).
+template <bool ASYNC, bool BATCH>
+__device__ void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
+                                const int32_t *R, int32_t *W, bool push, long long &mb, int window,
+                                uint32_t &phase)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    int *claim = &p.st->pass_tile[q & (kRing - 1)];
+    const long long n = in.n;
+    const int cpt = p.tile >> 5;
+    const bool ordered = ASYNC && op == OP_TENT;
+    const long long lim16 = (p.nnz * 4) & ~15ll;
+
+    int t = 0;
+    if (lane == 0) t = atomicAdd(claim, 1);
+    t = __shfl_sync(FULL_MASK, t, 0);
+    Chunk cur, nxt;
+    cur.tile = t;
+    cur.kin = 0;
+    cur.cb = ((long long)t * p.tile < n) ? (long long)t * p.tile : -1;
+    int slot = 0;
+    stage_chunk<BATCH>(p, sh, cur, n, slot, lane, wid, lim16);
+    while (cur.cb >= 0) {
+        nxt.tile = cur.tile;
+        nxt.kin = cur.kin + 1;
+        long long nb = (long long)nxt.tile * p.tile + (long long)nxt.kin * 32;
+        const bool last_of_tile = nxt.kin >= cpt || nb >= n;
+        if (last_of_tile) {
+            int t2 = 0;
+            if (lane == 0) t2 = atomicAdd(claim, 1);
+            t2 = __shfl_sync(FULL_MASK, t2, 0);
+            nxt.tile = t2;
+            nxt.kin = 0;
+            nb = (long long)t2 * p.tile;
+        }
+        nxt.cb = nb < n ? nb : -1;
+        PT_BEGIN(t_stage);
+        stage_chunk<BATCH>(p, sh, nxt, n, slot ^ 1, lane, wid, lim16);
+        PT_END(p.st, 0, t_stage);
+
+        bool staged = cur.soff >= 0;
+        PT_BEGIN(t_wait);
+        if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = false;
+        if (ordered && window > 0 && cur.kin == 0 && cur.tile >= window) wait_tile_done(p, cur.tile - window, lane);
+        PT_END(p.st, 1, t_wait);
+        PT_BEGIN(t_proc);
+        bool sus = false;
+        if (staged) {
+            const StagedEnts ent{sh.seg[wid][slot], cur.soff};
+            if (ordered)
+                sus = chunk_tent_ordered(p, ent, cur.cb, cur.v, cur.beg, cur.end, cur.nbase, W, mb, sh.warp_bm[wid],
+                                         lane, in.dmax);
+            else
+                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, cur.v, cur.beg, cur.end, cur.nbase, cur.g,
+                                        R, W, push, mb, lane, wid);
+        } else {
+            const GlobalEnts ent{p.col_idx};
+            if (ordered)
+                sus = chunk_tent_ordered(p, ent, cur.cb, cur.v, cur.beg, cur.end, cur.nbase, W, mb, sh.warp_bm[wid],
+                                         lane, in.dmax);
+            else
+                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, cur.v, cur.beg, cur.end, cur.nbase, cur.g,
+                                        R, W, push, mb, lane, wid);
+        }
+        // Round 0 with push: the suspects form the first repair worklist.
+        if (ordered && push) push_lanes<BATCH>(p, sus, cur.v, (int)(cur.end - cur.beg), cur.g, it, lane, false);
+        PT_END(p.st, ordered ? 2 : 3, t_proc);
+        if (ordered && window > 0 && last_of_tile) publish_tile_done(p, cur.tile, lane);
+        __syncwarp();  // every lane is done with seg[slot] before it is refilled
+        if ((threadIdx.x & 31) == 0) {
+#ifdef GC_PHASE_TIMING
+            atomicAdd(&p.st->dbg[4 + (staged ? 1 : 0)], 1ull);
+#endif
+        }
+        cur = nxt;
+        slot ^= 1;
+    }
+}
+
 // Runs `op` over the hubs (block per vertex) and then the tiles (warp per
 // 32 entries) of `in`.  Vertices found defective are appended to the
 // worklists of iteration `it` when `push` is set.
 template <bool ASYNC, bool BATCH>
 __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
-                         const int32_t *R, int32_t *W, bool push, long long &mb, int window = -1)
+                         const int32_t *R, int32_t *W, bool push, long long &mb, uint32_t &phase, int window = -1)
 {
     DevState *st = p.st;
     const int lane = threadIdx.x & 31;
@@ -614,7 +921,6 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
         st->pass_tile[(q + 2) & (kRing - 1)] = 0;
         st->pass_hub[(q + 2) & (kRing - 1)] = 0;
     }
-    int *out_wl = p.wl[it & 1];
     int *out_hub = p.hub[it & 1];
 
     // hubs: one block per vertex, longest tasks first
@@ -630,35 +936,24 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
-            const bool d = vertex_block<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh);
+            const bool d = vertex_block<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh) ||
+                           op == OP_TENT;  // round 0: hubs are kept for the first repair pass
             if (push && d && threadIdx.x == 0) {
                 atomicAdd(&st->wl_work[it & (kRing - 1)], (unsigned long long)(end - beg));
                 const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
                 if (idx < p.hub_cap) __stcg(out_hub + idx, v);
                 else atomicOr(&st->error, GC_EW_OVERFLOW);
-                note_push_graph<BATCH>(p, g, it);
+                if (op != OP_TENT) note_push_graph<BATCH>(p, g, it);
             }
         }
     }
 
     // tiles: one warp per group of `tile` consecutive worklist entries
-    int *claim = &st->pass_tile[q & (kRing - 1)];
-    if (ASYNC && op == OP_TENT && in.implicit) {
-        // Ordered tentative pass over V: tiles claimed in id order, lanes
-        // resolved in id order, at most `window` tiles in flight.
-        for (;;) {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(claim, 1);
-            t = __shfl_sync(FULL_MASK, t, 0);
-            const long long base = (long long)t * p.tile;
-            if (base >= in.n) break;
-            if (window > 0 && t >= window) wait_tile_done(p, t - window, lane);
-            for (int j = 0; j < p.tile && base + j < in.n; j += 32)
-                chunk_tent_ordered<BATCH>(p, base + j, W, mb, sh.warp_bm[wid], lane, in.dmax);
-            if (window > 0) publish_tile_done(p, t, lane);
-        }
+    if (in.implicit) {
+        implicit_staged<ASYNC, BATCH>(p, sh, op, q, it, in, R, W, push, mb, window, phase);
         return;
     }
+    int *claim = &st->pass_tile[q & (kRing - 1)];
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(claim, 1);
@@ -668,57 +963,18 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
         for (int j = 0; j < p.tile && base + j < in.n; j += 32) {
             const long long idx = base + j + lane;
             int32_t v = -1;
-            if (idx < in.n) v = in.implicit ? (int32_t)idx : __ldcg(in.wl + idx);
+            if (idx < in.n) v = __ldcg(in.wl + idx);
             int64_t beg = 0, end = 0;
             int32_t nbase = 0, g = 0;
             if (v >= 0) row_of<BATCH>(p, v, beg, end, nbase, g);
-            const int deg = (int)(end - beg);
-            if (in.implicit && deg > in.dmax) v = -1;  // coloured in another phase / stage
-            const bool mid = v >= 0 && deg > p.t1;
-            bool d = false;
-            if (v >= 0 && !mid) d = vertex_thread<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb);
-            unsigned mm = __ballot_sync(FULL_MASK, mid);
-            while (mm) {
-                const int src = __ffs(mm) - 1;
-                mm &= mm - 1;
-                const int32_t vv = __shfl_sync(FULL_MASK, v, src);
-                const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
-                const int64_t ee = __shfl_sync(FULL_MASK, end, src);
-                const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
-                const bool dd = vertex_warp<ASYNC>(p, op, vv, bb, ee, nb, R, W, in.implicit, mb,
-                                                   sh.warp_bm[wid], lane);
-                if (lane == src) d = dd;
-            }
-            if (push) {
-                const unsigned m = __ballot_sync(FULL_MASK, d);
-                if (m) {
-                    const int leader = __ffs(m) - 1;
-                    unsigned long long work = d ? (unsigned long long)deg : 0ull;
-                    for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(FULL_MASK, work, o);
-                    int ob = 0;
-                    if (lane == leader) {
-                        ob = atomicAdd(&st->wl_count[it & (kRing - 1)], __popc(m));
-                        atomicAdd(&st->wl_work[it & (kRing - 1)], work);
-                    }
-                    ob = __shfl_sync(FULL_MASK, ob, leader);
-                    if (d) {
-                        const int o = ob + __popc(m & ((1u << lane) - 1u));
-                        if (o < p.n) __stcg(out_wl + o, v);
-                        else atomicOr(&st->error, GC_EW_OVERFLOW);
-                        note_push_graph<BATCH>(p, g, it);
-                    }
-                }
-            }
+            chunk_ops<ASYNC, BATCH>(p, sh, GlobalEnts{p.col_idx}, op, it, false, in.dmax, v, beg, end, nbase, g, R,
+                                    W, push, mb, lane, wid);
         }
     }
 }
 
-// ------------------------------------------------------------------------
-// the colouring kernel
-// ------------------------------------------------------------------------
-
 template <bool ASYNC, bool BATCH>
-__global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
+__global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 {
     __shared__ Shared sh;
     DevState *st = p.st;
@@ -731,7 +987,15 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
     const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
     unsigned nbl = gridDim.x;
     long long mb = 0;
+    uint32_t phase = 0;  // parity bits of this warp's two staging barriers
+    if (lane == 0) {
+        mbar_init(&sh.mbar[threadIdx.x >> 5][0], 1);
+        mbar_init(&sh.mbar[threadIdx.x >> 5][1], 1);
+        fence_mbarrier_init();
+    }
+    __syncwarp();
 
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start = global_timer();
     if (ld_volatile(&st->error) == 0) {
         // Prologue: degree binning of V (hub list) and colour initialisation.
         // Deterministic round 0 colours every vertex from a snapshot in which
@@ -849,14 +1113,22 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
             if (in.n == 0 && in.hn == 0) continue;
             const bool last_stage = sg == nstages - 1;
             // Asynchronous round 0 (Algorithm 3): tentative colouring of the
-            // stage's vertices, in place on the current colours.
+            // stage's vertices, in place on the current colours.  Without
+            // snapshot rounds it also lists the vertices that can be in
+            // conflict afterwards, and the first repair round inspects only
+            // those (every other vertex of U^0 = V is provably clean).
             if (ASYNC && !twop) {
-                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, 0, in, R, R, false, mb, window);
+                const bool suspects = !snap;
+                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, window);
                 grid_sync(st, nbl);
+                if (blockIdx.x == 0 && threadIdx.x == 0 && it < kStamps) st->stamp[it] = global_timer();
                 if (ld_volatile(&st->error)) {
                     alive = false;
                     break;
                 }
+                if (suspects)
+                    in = PassIn{false, p.wl[it & 1], ld_volatile(&st->wl_count[it & (kRing - 1)]), p.hub[it & 1],
+                                ld_volatile(&st->hub_count[it & (kRing - 1)]), p.t2};
             }
             for (;;) {
                 ++it;
@@ -871,17 +1143,18 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
                     // the prologue), barrier, phase 2 detection, barrier.
                     if (ASYNC || it > 1) {
                         run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false,
-                                               mb, window);
+                                               mb, phase, window);
                         grid_sync(st, nbl);
                         if (ld_volatile(&st->error)) {
                             alive = false;
                             break;
                         }
                     }
-                    run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb);
+                    run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb,
+                                           phase);
                 } else {
                     // Algorithm 3: fused detect-and-recolour over U.
-                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb);
+                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb, phase);
                     last_written = W;
                 }
                 grid_sync(st, nbl);
@@ -893,6 +1166,7 @@ __global__ void __launch_bounds__(kBlock, 4) color_kernel(KParams p)
                 const int nh = ld_volatile(&st->hub_count[it & (kRing - 1)]);
                 const int tot = nl + nh;
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    if (it < kStamps) st->stamp[it] = global_timer();
                     st->rounds = it;
                     st->conflicts += (unsigned long long)tot;
                     if (p.round_sizes && it - 1 < p.round_sizes_cap) p.round_sizes[it - 1] = tot;

@@ -120,6 +120,8 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
         if (stats_out) {
             s.round_sizes = stats_out->round_sizes;
             s.round_sizes_cap = stats_out->round_sizes_cap;
+            s.round_ns = stats_out->round_ns;
+            s.round_ns_cap = stats_out->round_ns_cap;
             *stats_out = s;
         }
         return GC_OK;
@@ -214,6 +216,13 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
                 cudaGetLastError();
                 return GC_ERR_CUDA;
             }
+        }
+        s.round_ns = stats_out->round_ns;
+        s.round_ns_cap = stats_out->round_ns_cap;
+        if (s.round_ns && s.round_ns_cap > 0) {
+            int k = s.rounds + 1 < s.round_ns_cap ? s.rounds + 1 : s.round_ns_cap;
+            if (k > gc::kStamps) k = gc::kStamps;
+            for (int i = 0; i < k; ++i) s.round_ns[i] = h.stamp[i] ? (int64_t)(h.stamp[i] - h.t_start) : 0;
         }
         *stats_out = s;
     }

@@ -64,7 +64,8 @@ class gc_stats(ctypes.Structure):
                 ("conflicts", ctypes.c_int64), ("distinct_colors", ctypes.c_int32),
                 ("error_word", ctypes.c_int32), ("model_bytes", ctypes.c_int64),
                 ("elapsed_ms", ctypes.c_float), ("round_sizes", ctypes.c_void_p),
-                ("round_sizes_cap", ctypes.c_int32)]
+                ("round_sizes_cap", ctypes.c_int32), ("round_ns", ctypes.c_void_p),
+                ("round_ns_cap", ctypes.c_int32)]
 
 
 class gc_opts(ctypes.Structure):
@@ -181,13 +182,27 @@ def _opts(opts) -> gc_opts | None:
     return o
 
 
-def stats_dict(s: gc_stats, round_sizes=None) -> dict:
+def stats_dict(s: gc_stats, round_sizes=None, round_ns=None) -> dict:
     d = {"rounds": s.rounds, "colors": s.colors, "conflicts": s.conflicts,
          "distinct_colors": s.distinct_colors, "error_word": s.error_word,
          "model_bytes": s.model_bytes, "elapsed_ms": float(s.elapsed_ms)}
     if round_sizes is not None:
         d["round_sizes"] = round_sizes[: min(s.rounds, len(round_sizes))].copy()
+    if round_ns is not None:
+        d["round_ns"] = round_ns[: min(s.rounds + 1, len(round_ns))].copy()
     return d
+
+
+def _stats_buffers(st: gc_stats, round_cap: int):
+    if round_cap <= 0:
+        return None, None
+    rs = np.zeros(round_cap, np.int32)
+    rn = np.zeros(round_cap, np.int64)
+    st.round_sizes = rs.ctypes.data
+    st.round_sizes_cap = round_cap
+    st.round_ns = rn.ctypes.data
+    st.round_ns_cap = round_cap
+    return rs, rn
 
 
 def gc_ctx_create(device: int = 0) -> int:
@@ -210,14 +225,10 @@ def gc_color(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, round_ca
     _check_i32(colors_out, "colors_out")
     csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
     st = gc_stats()
-    rs = None
-    if round_cap > 0:
-        rs = np.zeros(round_cap, np.int32)
-        st.round_sizes = rs.ctypes.data
-        st.round_sizes_cap = round_cap
+    rs, rn = _stats_buffers(st, round_cap)
     rc = load().gc_color(ctypes.byref(csr), int(n), int(nnz), int(mode), _ptr(colors_out),
                          ctypes.byref(st))
-    return rc, stats_dict(st, rs)
+    return rc, stats_dict(st, rs, rn)
 
 
 def gc_color_async(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out,
@@ -233,13 +244,9 @@ def gc_color_async(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colo
 def gc_ctx_stats(ctx: int, round_cap: int = 0):
     """Wait for the context's last colouring; returns (status, stats dict)."""
     st = gc_stats()
-    rs = None
-    if round_cap > 0:
-        rs = np.zeros(round_cap, np.int32)
-        st.round_sizes = rs.ctypes.data
-        st.round_sizes_cap = round_cap
+    rs, rn = _stats_buffers(st, round_cap)
     rc = load().gc_ctx_stats(ctypes.c_void_p(ctx), ctypes.byref(st))
-    return int(rc), stats_dict(st, rs)
+    return int(rc), stats_dict(st, rs, rn)
 
 
 def gc_color_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, edge_off, row_ptr,
@@ -262,15 +269,11 @@ def gc_color_noalloc(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, 
     csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
     o = _opts(opts)
     st = gc_stats()
-    rs = None
-    if round_cap > 0:
-        rs = np.zeros(round_cap, np.int32)
-        st.round_sizes = rs.ctypes.data
-        st.round_sizes_cap = round_cap
+    rs, rn = _stats_buffers(st, round_cap)
     rc = load().gc_color_noalloc(ctypes.byref(csr), int(n), int(nnz), int(mode),
                                  ctypes.byref(o) if o is not None else None, _ptr(colors_out),
                                  ctypes.byref(st), ctypes.c_void_p(_stream_handle(stream)))
-    return int(rc), stats_dict(st, rs)
+    return int(rc), stats_dict(st, rs, rn)
 
 
 class Context:
