@@ -215,7 +215,8 @@ int gc_ctx_stats(gc_ctx *ctx, gc_stats *stats);
  *   col_idx: graph g's local (0-based) neighbour ids begin at
  *            col_idx + edge_off[g]
  * total_n = vtx_off[G] and total_nnz = edge_off[G] must be given on the
- * host as well.  Graph g's colours land at colors_out + vtx_off[g].
+ * host as well (total_n < 2^31, total_nnz < 2^33).  Graph g's colours land
+ * at colors_out + vtx_off[g].
  */
 typedef struct {
     int32_t G;

@@ -453,7 +453,9 @@ int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t *
 int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *opts, int32_t *colors_out,
                    int32_t *rounds_out, int64_t *conflicts_out, void *stream)
 {
-    if (!c || !b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0) return GC_ERR_ARG;
+    if (!c || !b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0 ||
+        b->total_nnz >= (1ll << gc::kWorkBits))
+        return GC_ERR_ARG;
     if (mode & ~(uint32_t)511) return GC_ERR_ARG;
     if (b->G > 0 && (!b->vtx_off || !b->edge_off)) return GC_ERR_ARG;
     if (b->total_n > 0 && (!b->row_ptr || !colors_out)) return GC_ERR_ARG;

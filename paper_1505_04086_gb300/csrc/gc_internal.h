@@ -23,6 +23,7 @@ constexpr int kLutShift = 10;           // batch: graph lookup per 1024 vertices
 constexpr int kRing = 4;                // round-counter ring depth
 constexpr int kStatBitmapWords = 1 << 15;  // distinct-colour bitmap: colours < 2^20
 constexpr int kStamps = 256;            // per-iteration end times kept in DevState
+constexpr int kWorkBits = 33;           // pushed-degree sum field of wl_packed (< 2^33 entries)
 constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
@@ -43,9 +44,10 @@ struct DevState {
     unsigned long long model_bytes;
     int pass_tile[kRing];      // per-pass claim counters (tiles)
     int pass_hub[kRing];       // per-pass claim counters (hubs)
-    int wl_count[kRing];       // per-iteration push counters (tile list)
     int hub_count[kRing];      // per-iteration push counters (hub list)
-    unsigned long long wl_work[kRing];  // per-iteration sum of degrees pushed
+    // per-iteration tile-list pushes: count << kWorkBits | sum of pushed
+    // degrees (tile and hub lists), one atomic per push
+    unsigned long long wl_packed[kRing];
     int distinct;
     unsigned long long dbg[16];      // phase cycle counters (builds with GC_PHASE_TIMING only)
     int window;                // round-0 in-flight window in tiles (-1: unlimited)

@@ -66,6 +66,12 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
 
+// Tile-list pushes of iteration `it` (read after the barrier that ends it).
+__device__ __forceinline__ int packed_count(DevState *st, int it)
+{
+    return (int)(*(volatile unsigned long long *)&st->wl_packed[it & (kRing - 1)] >> kWorkBits);
+}
+
 // mbarrier + 1-D bulk (TMA) copy helpers for staging adjacency segments.
 __device__ __forceinline__ uint32_t smem_addr(const void *ptr)
 {
@@ -117,10 +123,13 @@ __device__ __forceinline__ void fence_mbarrier_init() { asm volatile("fence.mbar
 // coherent (never served from a stale L1 line).  Deterministic mode never
 // reads a buffer that is written in the same round; it still bypasses L1
 // (.cg) because the buffer was written in an earlier round of this launch.
+#ifndef GC_ASYNC_LOAD
+#define GC_ASYNC_LOAD 0
+#endif
 template <bool ASYNC>
 __device__ __forceinline__ int ld_color(const int32_t *p)
 {
-    if (ASYNC) {
+    if (ASYNC && GC_ASYNC_LOAD == 0) {
         int v;
         asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
         return v;
@@ -716,10 +725,9 @@ __device__ __forceinline__ void push_lanes(const KParams &p, bool d, int32_t v, 
     unsigned long long work = d ? (unsigned long long)deg : 0ull;
     for (int o = 16; o > 0; o >>= 1) work += __shfl_xor_sync(FULL_MASK, work, o);
     int ob = 0;
-    if (lane == leader) {
-        ob = atomicAdd(&st->wl_count[it & (kRing - 1)], __popc(m));
-        atomicAdd(&st->wl_work[it & (kRing - 1)], work);
-    }
+    if (lane == leader)
+        ob = (int)(atomicAdd(&st->wl_packed[it & (kRing - 1)], ((unsigned long long)__popc(m) << kWorkBits) + work) >>
+                   kWorkBits);
     ob = __shfl_sync(FULL_MASK, ob, leader);
     if (d) {
         const int o = ob + __popc(m & ((1u << lane) - 1u));
@@ -939,7 +947,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             const bool d = vertex_block<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh) ||
                            op == OP_TENT;  // round 0: hubs are kept for the first repair pass
             if (push && d && threadIdx.x == 0) {
-                atomicAdd(&st->wl_work[it & (kRing - 1)], (unsigned long long)(end - beg));
+                atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
                 const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
                 if (idx < p.hub_cap) __stcg(out_hub + idx, v);
                 else atomicOr(&st->error, GC_EW_OVERFLOW);
@@ -1127,15 +1135,14 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                     break;
                 }
                 if (suspects)
-                    in = PassIn{false, p.wl[it & 1], ld_volatile(&st->wl_count[it & (kRing - 1)]), p.hub[it & 1],
+                    in = PassIn{false, p.wl[it & 1], packed_count(st, it), p.hub[it & 1],
                                 ld_volatile(&st->hub_count[it & (kRing - 1)]), p.t2};
             }
             for (;;) {
                 ++it;
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
-                    st->wl_count[(it + 2) & (kRing - 1)] = 0;
                     st->hub_count[(it + 2) & (kRing - 1)] = 0;
-                    st->wl_work[(it + 2) & (kRing - 1)] = 0;
+                    st->wl_packed[(it + 2) & (kRing - 1)] = 0;
                 }
                 if (twop) {
                     // Algorithm 2: phase 1 tentative colouring of U (in
@@ -1162,7 +1169,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                     copy_back = true;
                     break;
                 }
-                const int nl = ld_volatile(&st->wl_count[it & (kRing - 1)]);
+                const int nl = packed_count(st, it);
                 const int nh = ld_volatile(&st->hub_count[it & (kRing - 1)]);
                 const int tot = nl + nh;
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1183,7 +1190,8 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                     break;
                 }
                 in = PassIn{false, p.wl[it & 1], nl, p.hub[it & 1], nh, p.t2};
-                const unsigned long long work = *(volatile unsigned long long *)&st->wl_work[it & (kRing - 1)];
+                const unsigned long long work =
+                    *(volatile unsigned long long *)&st->wl_packed[it & (kRing - 1)] & ((1ull << kWorkBits) - 1);
                 if (last_stage && nbl > 1 && tot <= p.tail && work <= (unsigned long long)p.tail * kTailWorkPerVertex) {
                     // Few vertices left: block 0 finishes alone with block-local
                     // barriers; the others leave.
