@@ -148,10 +148,13 @@ typedef struct {
     int32_t window;              /* GC_SCHED_ASYNC round 0 (and the first
                                     tentative phase of Algorithm 2): at most
                                     this many tiles are coloured concurrently,
-                                    claimed in vertex order; 0 = automatic (1
-                                    when most edges join nearby ids, as in a
-                                    naturally numbered mesh, else unlimited),
-                                    -1 = unlimited */
+                                    claimed in vertex order.  0 = automatic:
+                                    a graph of at most 16384 vertices, or one
+                                    whose edges mostly join nearby ids (a
+                                    naturally numbered mesh), is coloured in id
+                                    order by one warp (sequential First-Fit);
+                                    other graphs without limit.  1 = every
+                                    graph in id order; -1 = no ordering */
 } gc_opts;
 
 typedef struct gc_ctx gc_ctx;
@@ -238,6 +241,69 @@ typedef struct {
 int gc_color_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, const gc_opts *opts,
                    int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
                    void *stream);
+
+/* ---- serving: continuous batching of colouring requests ------------------ */
+
+/*
+ * A colouring server on one device.  Requests (graphs in host memory) are
+ * queued; a worker thread admits them in arrival order while their CSR fits
+ * the device-memory budget (and at most max_slots are resident), uploading
+ * them on a copy stream, and whenever the GPU is free it colours all
+ * uploaded requests in one batched launch (gc_color_batch semantics, every
+ * graph independent).  Requests that arrive while a batch runs are uploaded
+ * meanwhile and join the next batch.  Thread-safe.
+ *
+ * Memory: the budget is one device allocation holding the resident graphs'
+ * row pointers and column indices ((n+1+nnz)*4 bytes each, 256-byte
+ * granules).  Per-batch working memory (about 32 bytes per vertex of the
+ * batch) comes on top of it, as does a pinned host pool of 2*budget bytes
+ * that holds submitted graphs and their results until they are polled
+ * (requests that do not fit it get pinned blocks of their own).
+ * In GC_SCHED_DET mode every request's colouring is exactly the colouring
+ * gc_color would return for it alone.
+ */
+typedef struct gc_server gc_server;
+
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t waves;              /* batched launches so far */
+    int64_t budget_bytes;        /* device bytes for resident graphs */
+    int64_t in_use_bytes;        /* of which held now */
+    int64_t peak_bytes;          /* most ever held (never above the budget) */
+    int32_t queued;              /* waiting for admission */
+    int32_t resident;            /* admitted and not finished */
+    int32_t max_wave_graphs;     /* largest batch launched */
+    int32_t pad;
+} gc_server_info;
+
+/* Create a server on `device` with a device-memory budget and a slot limit;
+ * mode and opts apply to every request (opts may be NULL). */
+int gc_server_create(gc_server **s, int device, size_t device_budget_bytes, int max_slots, uint32_t mode,
+                     const gc_opts *opts);
+
+/* Queue a graph given by HOST arrays; they are copied (to pinned memory)
+ * before the call returns, and the call does not wait for the GPU.  *ticket
+ * identifies the request.  GC_ERR_BUDGET if the graph alone can never fit
+ * the budget.  Results stay in pinned memory until polled. */
+int gc_server_submit(gc_server *s, const gc_csr *host_csr, int32_t n, int64_t nnz, uint64_t *ticket);
+
+/* GC_PENDING while the request runs; once done, copies its colours to the
+ * HOST array colors_out (n entries, may be NULL), fills stats_out (may be
+ * NULL; elapsed_ms = submit-to-completion latency, colors and
+ * distinct_colors counted on the host) and returns the request's status;
+ * the ticket is then released (GC_ERR_NOT_FOUND afterwards). */
+int gc_server_poll(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats *stats_out);
+
+/* As gc_server_poll, waiting up to timeout_ms (< 0: no limit) for the
+ * request to finish; GC_PENDING if it has not. */
+int gc_server_wait(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats *stats_out, int32_t timeout_ms);
+
+/* Counters and memory use of the server. */
+int gc_server_query(gc_server *s, gc_server_info *out);
+
+/* Stop the worker, wait for work in flight and free everything; requests
+ * not yet polled are dropped. */
+void gc_server_destroy(gc_server *s);
 
 /* ---- colouring without any allocation ---------------------------------- */
 

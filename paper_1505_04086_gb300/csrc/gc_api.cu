@@ -53,7 +53,7 @@ struct gc_ctx {
     int num_sms = 0;
     int occ[2][2] = {{0, 0}, {0, 0}};
     // scratch
-    Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done;
+    Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done, gstat, uofs, olist;
     Buf stage_rp, stage_ci, stage_col;  // gc_color host staging
     DevState *st_host = nullptr;        // pinned
     int32_t *rs_host = nullptr;         // pinned round sizes
@@ -111,6 +111,15 @@ int resolve_opts(const gc_opts *o, int64_t n, Resolved &r)
     return GC_OK;
 }
 
+int ensure_graph_tables(gc_ctx *c, int64_t G)
+{
+    const size_t g = (size_t)std::max<int64_t>(G, 1);
+    if (!c->gstat.reserve(g * sizeof(gc::GraphStat)) || !c->uofs.reserve((g + 1) * sizeof(int64_t)) ||
+        !c->olist.reserve(g * sizeof(int32_t)))
+        return GC_ERR_OOM;
+    return GC_OK;
+}
+
 int ensure_scratch(gc_ctx *c, int64_t n, bool need_b, bool batch, int64_t lut_entries)
 {
     const size_t vb = (size_t)std::max<int64_t>(n, 1) * sizeof(int32_t);
@@ -156,6 +165,9 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.tail = r.tail;
     p.window = r.window;
     p.done = c->done.as<int32_t>();
+    p.gstat = c->gstat.as<gc::GraphStat>();
+    p.uofs = c->uofs.as<int64_t>();
+    p.olist = c->olist.as<int32_t>();
     p.cB = c->cB.as<int32_t>();
     p.wl[0] = c->wl0.as<int32_t>();
     p.wl[1] = c->wl1.as<int32_t>();
@@ -166,6 +178,8 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.hub_cap = (int32_t)n;
 
     if ((e = cudaMemsetAsync(c->st.p, 0, sizeof(DevState), s)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(c->gstat.p, 0, (size_t)std::max(p.G, 1) * sizeof(gc::GraphStat), s)) != cudaSuccess)
+        return cuda_status(e);
     const bool stats = !(mode & GC_NO_COLOR_STATS);
     if (stats && (e = cudaMemsetAsync(c->bitmap.p, 0, gc::kStatBitmapWords * sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_status(e);
@@ -221,6 +235,77 @@ gc_ctx *default_ctx()
 }
 
 }  // namespace
+
+namespace gc {
+
+int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, const int64_t *vtx_off,
+                     const int64_t *edge_off, const int64_t *rp_off, const int32_t *row_ptr, const int32_t *col_idx,
+                     uint32_t mode, const gc_opts *opts, int32_t *colors_out, int32_t *rounds_out,
+                     int64_t *conflicts_out, cudaStream_t s)
+{
+    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
+    if (total_n > 0 && !colors_out) return GC_ERR_ARG;
+    Resolved r;
+    // The cap applies per graph; every graph's own bound is below total_n + 1.
+    int rc = resolve_opts(opts, total_n, r);
+    if (rc != GC_OK) return rc;
+    c->pending = false;
+    c->last_n = (int32_t)total_n;
+    c->last_mode = mode;
+    c->last_empty = (total_n == 0);
+    c->launch_status = GC_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return GC_ERR_CUDA;
+    if (G > 0 && rounds_out) {
+        cudaError_t e = cudaMemsetAsync(rounds_out, 0, (size_t)G * sizeof(int32_t), s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (G > 0 && conflicts_out) {
+        cudaError_t e = cudaMemsetAsync(conflicts_out, 0, (size_t)G * sizeof(int64_t), s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (total_n == 0) {
+        c->pending = true;
+        return GC_OK;
+    }
+    const bool async = (mode & GC_SCHED_ASYNC) != 0;
+    const int64_t n = total_n;
+    const int64_t lut_entries = (n + (1 << kLutShift) - 1) >> kLutShift;
+    const bool need_b = !async || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE));
+    if ((rc = ensure_scratch(c, n, need_b, true, lut_entries)) != GC_OK) return rc;
+    if ((rc = ensure_graph_tables(c, G)) != GC_OK) return rc;
+    KParams p;
+    memset(&p, 0, sizeof p);
+    p.row_ptr = row_ptr;
+    p.col_idx = col_idx;
+    p.vtx_off = vtx_off;
+    p.edge_off = edge_off;
+    p.rp_off = rp_off;
+    p.gid_lut = c->lut.as<int32_t>();
+    p.G = G;
+    p.n = (int32_t)n;
+    p.nnz = total_nnz;
+    p.cA = colors_out;
+    p.g_rounds = rounds_out;
+    p.g_conflicts = reinterpret_cast<unsigned long long *>(conflicts_out);
+    rc = enqueue(c, p, true, mode, r, s);
+    if (rc == GC_OK) c->pending = true;
+    c->launch_status = rc;
+    return rc;
+}
+
+int color_batch_offsets(gc_ctx *ctx, int32_t G, int64_t total_n, int64_t col_extent, const int64_t *vtx_off,
+                        const int64_t *edge_off, const int64_t *rp_off, const int32_t *base, uint32_t mode,
+                        const gc_opts *opts, int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
+                        cudaStream_t stream)
+{
+    if (!ctx || G < 0 || total_n < 0 || total_n > INT32_MAX || col_extent < 0 ||
+        col_extent >= (1ll << kWorkBits) || (G > 0 && (!vtx_off || !edge_off || !rp_off || !base)))
+        return GC_ERR_ARG;
+    return color_batch_impl(ctx, G, total_n, col_extent, vtx_off, edge_off, rp_off, base, base, mode, opts,
+                            colors_out, rounds_out, conflicts_out, stream);
+}
+
+}  // namespace gc
 
 extern "C" {
 
@@ -296,7 +381,8 @@ void gc_ctx_destroy(gc_ctx *c)
     cudaSetDevice(c->device);
     if (c->ev_done) cudaEventSynchronize(c->ev_done);
     for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
-                   &c->round_sizes, &c->st, &c->done, &c->stage_rp, &c->stage_ci, &c->stage_col})
+                   &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->stage_rp, &c->stage_ci,
+                   &c->stage_col})
         b->release();
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->rs_host) cudaFreeHost(c->rs_host);
@@ -331,6 +417,7 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
     const bool async = (mode & GC_SCHED_ASYNC) != 0;
     const bool need_b = !async || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE));
     if ((rc = ensure_scratch(c, n, need_b, false, 0)) != GC_OK) return rc;
+    if ((rc = ensure_graph_tables(c, 1)) != GC_OK) return rc;
     KParams p;
     memset(&p, 0, sizeof p);
     p.row_ptr = csr->row_ptr;
@@ -456,56 +543,11 @@ int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o
     if (!c || !b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0 ||
         b->total_nnz >= (1ll << gc::kWorkBits))
         return GC_ERR_ARG;
-    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
     if (b->G > 0 && (!b->vtx_off || !b->edge_off)) return GC_ERR_ARG;
-    if (b->total_n > 0 && (!b->row_ptr || !colors_out)) return GC_ERR_ARG;
+    if (b->total_n > 0 && !b->row_ptr) return GC_ERR_ARG;
     if (b->total_nnz > 0 && !b->col_idx) return GC_ERR_ARG;
-    Resolved r;
-    // The cap applies per graph; every graph's own bound is below total_n + 1.
-    int rc = resolve_opts(opts, b->total_n, r);
-    if (rc != GC_OK) return rc;
-    if (r.window == 0) r.window = -1;  // a global tile order would serialise the graphs
-    c->pending = false;
-    c->last_n = (int32_t)b->total_n;
-    c->last_mode = mode;
-    c->last_empty = (b->total_n == 0);
-    c->launch_status = GC_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaSetDevice(c->device) != cudaSuccess) return GC_ERR_CUDA;
-    if (b->G > 0 && rounds_out) {
-        cudaError_t e = cudaMemsetAsync(rounds_out, 0, (size_t)b->G * sizeof(int32_t), s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    if (b->G > 0 && conflicts_out) {
-        cudaError_t e = cudaMemsetAsync(conflicts_out, 0, (size_t)b->G * sizeof(int64_t), s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    if (b->total_n == 0) {
-        c->pending = true;
-        return GC_OK;
-    }
-    const bool async = (mode & GC_SCHED_ASYNC) != 0;
-    const int64_t n = b->total_n;
-    const int64_t lut_entries = (n + (1 << gc::kLutShift) - 1) >> gc::kLutShift;
-    const bool need_b = !async || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE));
-    if ((rc = ensure_scratch(c, n, need_b, true, lut_entries)) != GC_OK) return rc;
-    KParams p;
-    memset(&p, 0, sizeof p);
-    p.row_ptr = b->row_ptr;
-    p.col_idx = b->col_idx;
-    p.vtx_off = b->vtx_off;
-    p.edge_off = b->edge_off;
-    p.gid_lut = c->lut.as<int32_t>();
-    p.G = b->G;
-    p.n = (int32_t)n;
-    p.nnz = b->total_nnz;
-    p.cA = colors_out;
-    p.g_rounds = rounds_out;
-    p.g_conflicts = reinterpret_cast<unsigned long long *>(conflicts_out);
-    rc = enqueue(c, p, true, mode, r, s);
-    if (rc == GC_OK) c->pending = true;
-    c->launch_status = rc;
-    return rc;
+    return gc::color_batch_impl(c, b->G, b->total_n, b->total_nnz, b->vtx_off, b->edge_off, nullptr, b->row_ptr,
+                                b->col_idx, mode, opts, colors_out, rounds_out, conflicts_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

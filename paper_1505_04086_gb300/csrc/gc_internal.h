@@ -19,17 +19,28 @@ constexpr int kHubBmWords = 256;        // block path: 8192-colour window per pa
 #define GC_SEG_CAP 512
 #endif
 constexpr int kSegCap = GC_SEG_CAP;     // staged adjacency entries per buffer (2 per warp)
+constexpr int kRingIds = 1024;          // ordered graphs: colours of the last ids, per warp
 constexpr int kLutShift = 10;           // batch: graph lookup per 1024 vertices
 constexpr int kRing = 4;                // round-counter ring depth
 constexpr int kStatBitmapWords = 1 << 15;  // distinct-colour bitmap: colours < 2^20
 constexpr int kStamps = 256;            // per-iteration end times kept in DevState
 constexpr int kWorkBits = 33;           // pushed-degree sum field of wl_packed (< 2^33 entries)
 constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
-constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
+constexpr int kNearIds = 2048;
+constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)          // locality: "near" lower neighbour id distance
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 enum Tie : int { TIE_LOWER = 0, TIE_HIGHER = 1, TIE_NONE = 2 };
+
+// Per-graph state of one launch (a single graph is graph 0).  Zeroed
+// before each launch.
+struct GraphStat {
+    unsigned long long near_lower;  // locality sample: lower neighbours within kNearIds
+    unsigned long long all_lower;   // locality sample: all lower neighbours
+    unsigned int hubs;              // vertices of degree > t2
+    unsigned int ordered;           // coloured in id order by one warp in round 0
+};
 
 // Device-resident state of one colouring launch.  Zeroed before each launch.
 struct DevState {
@@ -50,9 +61,10 @@ struct DevState {
     unsigned long long wl_packed[kRing];
     int distinct;
     unsigned long long dbg[16];      // phase cycle counters (builds with GC_PHASE_TIMING only)
-    int window;                // round-0 in-flight window in tiles (-1: unlimited)
-    unsigned long long near_lower;   // locality sample: lower neighbours within kNearIds
-    unsigned long long all_lower;    // locality sample: all lower neighbours
+    int seq_claim;                   // round 0: next ordered graph to claim
+    int n_ordered;                   // number of ordered graphs
+    long long n_uchunks;             // chunks of the graphs that are not ordered
+    int window;                      // number of graphs coloured in id order in round 0
     unsigned long long t_start;      // globaltimer at kernel start (ns)
     unsigned long long stamp[kStamps];  // [0]: end of round 0, [k]: end of iteration k
 };
@@ -64,6 +76,8 @@ struct KParams {
     const int64_t *vtx_off;
     const int64_t *edge_off;
     const int32_t *gid_lut;
+    const int64_t *rp_off;     // batch: graph g's row pointers start at row_ptr + rp_off[g]
+                               // (null: at row_ptr + vtx_off[g] + g)
     int32_t G;
     int32_t n;                 // total vertices
     int64_t nnz;               // total entries
@@ -89,12 +103,26 @@ struct KParams {
     int32_t tail;
     int32_t window;            // asynchronous round 0: tiles in flight (0 auto, -1 unlimited)
     int32_t *done;             // per-tile completion flags of the ordered round-0 pass
+    GraphStat *gstat;          // G entries (1 for a single graph)
+    int64_t *uofs;             // G+1: prefix sums of the unordered graphs' chunk counts
+    int32_t *olist;            // G: the ordered graphs
 };
+
+// Batched colouring with per-graph row-pointer offsets (the server's waves:
+// every graph's arrays sit at its own offset in one device arena).
+// base: arena start (row pointers and column indices are read relative to
+// it); col_extent: int32 entries readable from base.  Same contract as
+// gc_color_batch otherwise; finish with gc_ctx_stats.
+int color_batch_offsets(gc_ctx *ctx, int32_t G, int64_t total_n, int64_t col_extent, const int64_t *vtx_off,
+                        const int64_t *edge_off, const int64_t *rp_off, const int32_t *base, uint32_t mode,
+                        const gc_opts *opts, int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
+                        cudaStream_t stream);
 
 // Launchers (gc_kernels.cu).  All return cudaSuccess or the launch error.
 cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s);
 cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm);
 size_t color_smem_bytes();
+cudaError_t prepare_color_kernels();  // opt in to the kernel's dynamic shared memory
 cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, uint32_t *bitmap,
                                int grid, cudaStream_t s);
 cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s);

@@ -204,7 +204,7 @@ __device__ __forceinline__ void row_of(const KParams &p, int32_t v, int64_t &beg
         while (gg + 1 < p.G && __ldg(p.vtx_off + gg + 1) <= (int64_t)v) ++gg;
         const int64_t vo = __ldg(p.vtx_off + gg);
         const int64_t eo = __ldg(p.edge_off + gg);
-        const int32_t *rp = p.row_ptr + vo + gg;
+        const int32_t *rp = p.row_ptr + (p.rp_off ? __ldg(p.rp_off + gg) : vo + gg);
         const int32_t lv = v - (int32_t)vo;
         beg = eo + __ldg(rp + lv);
         end = eo + __ldg(rp + lv + 1);
@@ -226,9 +226,12 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_THREAD_UNROLL 8
 #endif
 #ifndef GC_MIN_BLOCKS
-#define GC_MIN_BLOCKS 4
+#define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
+#ifndef GC_PASS_INLINE
+#define GC_PASS_INLINE __forceinline__
+#endif
 
 // Adjacency entry k (a global CSR index) of the row being processed: read
 // from col_idx, or from the warp's staged copy of the chunk's segment.
@@ -410,7 +413,7 @@ __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t en
 }
 
 template <bool ASYNC>
-__device__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+__device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
                             const int32_t *R, int32_t *W, bool implicit, long long &mb, uint32_t *bm,
                             int lane)
 {
@@ -448,7 +451,14 @@ __device__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, in
 
 struct Shared {
     int32_t seg[kWarps][2][kSegCap];         // staged adjacency segments (double buffer per warp)
+    uint16_t ring[kWarps][kRingIds];         // ordered graphs: colours of the warp's last ids
     unsigned long long mbar[kWarps][2];      // their completion barriers
+    struct SlotInfo {
+        long long cb;                        // first id of the chunk; -1: none
+        long long cend;                      // ids of the chunk stop here
+        long long soff;                      // entry index held by seg[..][0]; -1: not staged
+        int tile, kin;                       // claimed tile and chunk index inside it
+    } slot[kWarps][2];
     uint32_t warp_bm[kWarps][kWarpBmWords];
     uint32_t hub_bm[kHubBmWords];
     int first;
@@ -535,7 +545,7 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
 }
 
 template <bool ASYNC>
-__device__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+__device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
                              const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh)
 {
     const int deg = (int)(end - beg);
@@ -579,10 +589,16 @@ __device__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, i
 // Returns true on lanes whose vertex may end round 0 in conflict with a
 // neighbour it can lose to (see `suspect` below); such vertices form the
 // first repair worklist instead of all of V.
-template <class E>
+constexpr uint16_t kRingGlobal = 0xFFFFu;  // ring entry: read this id's colour from memory
+
+// RING: the chunk belongs to an ordered graph that this warp colours in id
+// order from v0; ids in [max(v0, cbase - kRingIds), cbase) were coloured by
+// this warp and their colours sit in `ring`; with skip_higher no id above
+// the chunk is coloured yet (the graph has no vertex coloured elsewhere).
+template <class E, bool RING>
 __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cbase, int32_t v, int64_t beg,
                                    int64_t end, int32_t nbase, int32_t *C, long long &mb, uint32_t *bm, int lane,
-                                   int dmax)
+                                   int dmax, uint16_t *ring = nullptr, long long v0 = 0, bool skip_higher = false)
 {
     const int deg = (int)(end - beg);
     const int tie = p.tie;
@@ -615,8 +631,27 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
                 outside[q] = u[q] >= 0 && !inside;
             }
             int c[kUnroll];
+            if (RING) {
+                bool glob[kUnroll];
 #pragma unroll
-            for (int q = 0; q < kUnroll; ++q) c[q] = outside[q] ? ld_color<true>(C + u[q]) : 0;
+                for (int q = 0; q < kUnroll; ++q) {
+                    glob[q] = outside[q];
+                    c[q] = 0;
+                    if (outside[q] && u[q] < cbase && u[q] >= v0 && cbase - u[q] <= kRingIds) {
+                        const uint16_t r = ring[u[q] & (kRingIds - 1)];
+                        glob[q] = r == kRingGlobal;
+                        c[q] = r;
+                    } else if (outside[q] && skip_higher && u[q] >= cbase + 32) {
+                        glob[q] = false;  // not coloured yet in id order
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q)
+                    if (glob[q]) c[q] = ld_color<true>(C + u[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) c[q] = outside[q] ? ld_color<true>(C + u[q]) : 0;
+            }
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
                 const unsigned b = (unsigned)(c[q] - 1);
@@ -658,6 +693,19 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         const int64_t ee = __shfl_sync(FULL_MASK, end, src);
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
         vertex_warp<true>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane);
+    }
+    if (RING) {
+        __syncwarp();
+        if (v >= 0) {
+            uint16_t r = kRingGlobal;
+            if (thr) r = (uint16_t)mine;
+            else if (mid) {
+                const int cm = ld_color<true>(C + v);
+                r = cm < (int)kRingGlobal ? (uint16_t)cm : kRingGlobal;
+            }
+            ring[v & (kRingIds - 1)] = r;
+        }
+        __syncwarp();
     }
     return suspect;
 }
@@ -766,51 +814,61 @@ __device__ __forceinline__ void chunk_ops(const KParams &p, Shared &sh, const E 
     if (push) push_lanes<BATCH>(p, d, v, deg, g, it, lane, true);
 }
 
-// A chunk of 32 consecutive ids in a pass over V, with its rows and (when
-// its adjacency segment fits a buffer) a bulk copy of that segment in flight.
-struct Chunk {
-    long long cb;              // first id; -1: no chunk
-    int tile, kin;             // claimed tile and chunk index inside it
-    int32_t v, nbase, g;       // lane's vertex (-1: none) and graph
-    int64_t beg, end;          // lane's row
-    int64_t soff;              // entry index held by seg[slot][0]; -1: not staged
+// A chunk of 32 consecutive ids in a pass over V: its uniform description
+// lives in Shared::slot, each lane's row in a LaneRow register set.
+struct LaneRow {
+    int64_t beg;               // lane's row starts here (entry index)
+    int32_t deg;               // and holds deg entries; -1: no vertex on this lane
+    int32_t nbase, g;          // batch: graph offset and graph (0 otherwise)
 };
 
 constexpr unsigned kStagePolls = 1u << 22;
 
-// Load the lanes' row pointers of chunk c and start the 1-D TMA copy of the
-// chunk's contiguous adjacency segment into seg[wid][slot].  The copy runs
+// Load the lanes' row pointers of chunk [cb, min(cb+32, cend)) into `r`,
+// record the chunk in Shared::slot[wid][slot] and start the 1-D TMA copy of
+// its contiguous adjacency segment into seg[wid][slot].  The copy runs
 // 16-byte aligned; a segment that does not fit, or whose aligned end would
 // pass the last full 16 bytes of col_idx, is read from global memory instead.
 template <bool BATCH>
-__device__ __forceinline__ void stage_chunk(const KParams &p, Shared &sh, Chunk &c, long long n, int slot,
-                                            int lane, int wid, long long lim16)
+__device__ __forceinline__ void stage_chunk(const KParams &p, Shared &sh, long long cb, long long cend, int tile,
+                                            int kin, int slot, int lane, int wid, long long lim16, LaneRow &r)
 {
-    c.v = -1;
-    c.beg = c.end = 0;
-    c.nbase = 0;
-    c.g = 0;
-    c.soff = -1;
-    if (c.cb < 0) return;
-    const long long vi = c.cb + lane;
-    if (vi < n) {
-        c.v = (int32_t)vi;
-        row_of<BATCH>(p, c.v, c.beg, c.end, c.nbase, c.g);
-    }
-    const int last = (int)min(31ll, n - 1 - c.cb);
-    const long long s0 = __shfl_sync(FULL_MASK, (long long)c.beg, 0);
-    const long long e0 = __shfl_sync(FULL_MASK, (long long)c.end, last);
-    const long long a0 = (s0 * 4) & ~15ll;
-    const long long a1 = (e0 * 4 + 15) & ~15ll;
-    if (e0 > s0 && a1 - a0 <= (long long)kSegCap * 4 && a1 <= lim16) {
-        c.soff = a0 >> 2;
-        if (lane == 0) {
-            fence_proxy_async_smem();  // earlier reads of this buffer precede the copy
-            mbar_arrive_expect_tx(&sh.mbar[wid][slot], (uint32_t)(a1 - a0));
-            bulk_copy_g2s(sh.seg[wid][slot], reinterpret_cast<const char *>(p.col_idx) + a0, (uint32_t)(a1 - a0),
-                          &sh.mbar[wid][slot]);
+    r.beg = 0;
+    r.deg = -1;
+    r.nbase = 0;
+    r.g = 0;
+    long long soff = -1;
+    if (cb >= 0) {
+        const long long vi = cb + lane;
+        if (vi < cend) {
+            int64_t end;
+            row_of<BATCH>(p, (int32_t)vi, r.beg, end, r.nbase, r.g);
+            r.deg = (int32_t)(end - r.beg);
+        }
+        const int last = (int)min(31ll, cend - 1 - cb);
+        const long long s0 = __shfl_sync(FULL_MASK, (long long)r.beg, 0);
+        const long long e0 = __shfl_sync(FULL_MASK, (long long)(r.beg + (r.deg > 0 ? r.deg : 0)), last);
+        const long long a0 = (s0 * 4) & ~15ll;
+        const long long a1 = (e0 * 4 + 15) & ~15ll;
+        if (e0 > s0 && a1 - a0 <= (long long)kSegCap * 4 && a1 <= lim16) {
+            soff = a0 >> 2;
+            if (lane == 0) {
+                fence_proxy_async_smem();  // earlier reads of this buffer precede the copy
+                mbar_arrive_expect_tx(&sh.mbar[wid][slot], (uint32_t)(a1 - a0));
+                bulk_copy_g2s(sh.seg[wid][slot], reinterpret_cast<const char *>(p.col_idx) + a0, (uint32_t)(a1 - a0),
+                              &sh.mbar[wid][slot]);
+            }
         }
     }
+    if (lane == 0) {
+        Shared::SlotInfo &si = sh.slot[wid][slot];
+        si.cb = cb;
+        si.cend = cend;
+        si.soff = soff;
+        si.tile = tile;
+        si.kin = kin;
+    }
+    __syncwarp();
 }
 
 // Bounded wait for the copy into seg[wid][slot]; on timeout the error word
@@ -832,84 +890,227 @@ __device__ __forceinline__ bool wait_stage(const KParams &p, Shared &sh, int slo
     return true;
 }
 
+// Round 0 of an ordered graph (ids v0..v1-1): one warp colours it chunk by
+// chunk in id order, each chunk's lanes in id order, which is exactly
+// sequential First-Fit (Algorithm 1) on the graph apart from vertices
+// coloured elsewhere (hubs, earlier tiers).  Chunk j+1's segment is staged
+// while chunk j is worked on; recent colours are read from the warp's ring.
+template <bool BATCH>
+__device__ __noinline__ void seq_graph(const KParams &p, Shared &sh, int32_t g, long long v0, long long v1,
+                                       int32_t *C, long long &mb, uint32_t &phase, int lane, int wid, int dmax,
+                                       bool skip_higher, int it, bool push)
+{
+    const long long lim16 = (p.nnz * 4) & ~15ll;
+    uint16_t *ring = sh.ring[wid];
+    // The graph's row pointers and column indices (local ids + nbase).
+    const int32_t *rp = p.row_ptr;
+    int64_t eo = 0;
+    int32_t nbase = 0;
+    if (BATCH) {
+        rp = p.row_ptr + (p.rp_off ? __ldg(p.rp_off + g) : v0 + g);
+        eo = __ldg(p.edge_off + g);
+        nbase = (int32_t)v0;
+    }
+    const long long ng = v1 - v0;
+    // Row pointers are loaded two chunks ahead, the segment copy one ahead.
+    auto load_rows = [&](long long k, int32_t &b, int32_t &e) {
+        const long long lv = k * 32 + lane;
+        b = e = 0;
+        if (k >= 0 && lv < ng) {
+            b = __ldg(rp + lv);
+            e = __ldg(rp + lv + 1);
+        }
+    };
+    auto issue = [&](long long k, int slot, int32_t b, int32_t e) -> long long {
+        // start the copy of chunk k's segment; returns soff (-1: not staged)
+        long long soff = -1;
+        if (k * 32 < ng) {
+            const int last = (int)min(31ll, ng - 1 - k * 32);
+            const long long s0 = eo + __shfl_sync(FULL_MASK, b, 0);
+            const long long e0 = eo + __shfl_sync(FULL_MASK, e, last);
+            const long long a0 = (s0 * 4) & ~15ll, a1 = (e0 * 4 + 15) & ~15ll;
+            if (e0 > s0 && a1 - a0 <= (long long)kSegCap * 4 && a1 <= lim16) {
+                soff = a0 >> 2;
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&sh.mbar[wid][slot], (uint32_t)(a1 - a0));
+                    bulk_copy_g2s(sh.seg[wid][slot], reinterpret_cast<const char *>(p.col_idx) + a0,
+                                  (uint32_t)(a1 - a0), &sh.mbar[wid][slot]);
+                }
+            }
+        }
+        return soff;
+    };
+    const long long nck = (ng + 31) / 32;
+    int32_t b0, e0, b1, e1, b2, e2;
+    load_rows(0, b0, e0);
+    load_rows(1, b1, e1);
+    int slot = 0;
+    long long soff0 = nck > 0 ? issue(0, 0, b0, e0) : -1;
+    for (long long k = 0; k < nck; ++k) {
+        PT_BEGIN(t_iss);
+        load_rows(k + 2, b2, e2);
+        const long long soff1 = k + 1 < nck ? issue(k + 1, slot ^ 1, b1, e1) : -1;
+        PT_END(p.st, 11, t_iss);
+        bool staged = soff0 >= 0;
+        PT_BEGIN(t_w);
+        if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = false;
+        PT_END(p.st, 9, t_w);
+        PT_BEGIN(t_pr);
+        const long long cb = v0 + k * 32;
+        const int32_t v = k * 32 + lane < ng ? (int32_t)(cb + lane) : -1;
+        const int64_t beg = eo + b0, end = eo + e0;
+        bool sus;
+        if (staged)
+            sus = chunk_tent_ordered<StagedEnts, true>(p, StagedEnts{sh.seg[wid][slot], soff0}, cb, v, beg, end,
+                                                       nbase, C, mb, sh.warp_bm[wid], lane, dmax, ring, v0,
+                                                       skip_higher);
+        else
+            sus = chunk_tent_ordered<GlobalEnts, true>(p, GlobalEnts{p.col_idx}, cb, v, beg, end, nbase, C, mb,
+                                                       sh.warp_bm[wid], lane, dmax, ring, v0, skip_higher);
+        if (push) push_lanes<BATCH>(p, sus, v, e0 - b0, g, it, lane, false);
+        __syncwarp();
+        PT_END(p.st, 10, t_pr);
+        b0 = b1;
+        e0 = e1;
+        b1 = b2;
+        e1 = e2;
+        soff0 = soff1;
+        slot ^= 1;
+    }
+}
+
+// Chunk vc of a pass: direct (ids 32*vc.., up to n) or, in the round-0
+// tentative pass, numbered over the graphs that are not ordered (uofs holds
+// their prefix sums of chunk counts).
+template <bool BATCH>
+__device__ __forceinline__ void chunk_of(const KParams &p, long long vc, bool virt, long long n, long long &cb,
+                                         long long &cend)
+{
+    if (!virt) {
+        cb = vc * 32;
+        cend = n;
+        return;
+    }
+    if (!BATCH) {
+        cb = vc * 32;
+        cend = p.n;
+        return;
+    }
+    int lo = 0, hi = p.G - 1;  // largest g with uofs[g] <= vc
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldcg(p.uofs + mid) <= vc) lo = mid;
+        else hi = mid - 1;
+    }
+    cb = __ldg(p.vtx_off + lo) + (vc - __ldcg(p.uofs + lo)) * 32;
+    cend = __ldg(p.vtx_off + lo + 1);
+}
+
 // Pass over all of V (implicit worklist): each warp walks the chunks of the
 // tiles it claims in id order, staging chunk j+1 while it works on chunk j.
 // The asynchronous tentative pass resolves lanes in id order and keeps at
 // most `window` tiles in flight (window <= 0: no limit).
 template <bool ASYNC, bool BATCH>
-__device__ void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
+__device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
                                 const int32_t *R, int32_t *W, bool push, long long &mb, int window,
                                 uint32_t &phase)
 {
+    DevState *st = p.st;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    int *claim = &p.st->pass_tile[q & (kRing - 1)];
+    int *claim = &st->pass_tile[q & (kRing - 1)];
     const long long n = in.n;
     const int cpt = p.tile >> 5;
     const bool ordered = ASYNC && op == OP_TENT;
     const long long lim16 = (p.nnz * 4) & ~15ll;
 
+    if (ordered) {
+        // Phase A: ordered graphs, one warp each, largest work first claimed.
+        const int nord = ld_volatile(&st->n_ordered);
+        const bool tiered = (p.mode & GC_TIERS) != 0;
+        for (;;) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&st->seq_claim, 1);
+            k = __shfl_sync(FULL_MASK, k, 0);
+            if (k >= nord) break;
+            const int g = __ldcg(p.olist + k);
+            const long long v0 = BATCH ? __ldg(p.vtx_off + g) : 0;
+            const long long v1 = BATCH ? __ldg(p.vtx_off + g + 1) : p.n;
+            const bool skip_higher = !tiered && __ldcg(&p.gstat[g].hubs) == 0;
+            seq_graph<BATCH>(p, sh, g, v0, v1, W, mb, phase, lane, wid, in.dmax, skip_higher, it, push);
+        }
+    }
+    // Phase B: chunks claimed tile by tile (the unordered graphs only, in the
+    // round-0 tentative pass).
+    const long long nchunks = ordered ? *(volatile long long *)&st->n_uchunks : (n + 31) / 32;
+    const long long ntiles = (nchunks + cpt - 1) / cpt;
+
     int t = 0;
     if (lane == 0) t = atomicAdd(claim, 1);
     t = __shfl_sync(FULL_MASK, t, 0);
-    Chunk cur, nxt;
-    cur.tile = t;
-    cur.kin = 0;
-    cur.cb = ((long long)t * p.tile < n) ? (long long)t * p.tile : -1;
+    LaneRow cur, nxt;
     int slot = 0;
-    stage_chunk<BATCH>(p, sh, cur, n, slot, lane, wid, lim16);
-    while (cur.cb >= 0) {
-        nxt.tile = cur.tile;
-        nxt.kin = cur.kin + 1;
-        long long nb = (long long)nxt.tile * p.tile + (long long)nxt.kin * 32;
-        const bool last_of_tile = nxt.kin >= cpt || nb >= n;
+    {
+        long long cb = -1, cend = 0;
+        if (t < ntiles) chunk_of<BATCH>(p, (long long)t * cpt, ordered, n, cb, cend);
+        stage_chunk<BATCH>(p, sh, cb, cend, t, 0, slot, lane, wid, lim16, cur);
+    }
+    for (;;) {
+        const long long cb = sh.slot[wid][slot].cb;
+        if (cb < 0) break;
+        const long long soff = sh.slot[wid][slot].soff;
+        const int tile = sh.slot[wid][slot].tile;
+        const int kin = sh.slot[wid][slot].kin;
+        int ntile = tile, nkin = kin + 1;
+        long long vc = (long long)ntile * cpt + nkin;
+        const bool last_of_tile = nkin >= cpt || vc >= nchunks;
         if (last_of_tile) {
             int t2 = 0;
             if (lane == 0) t2 = atomicAdd(claim, 1);
-            t2 = __shfl_sync(FULL_MASK, t2, 0);
-            nxt.tile = t2;
-            nxt.kin = 0;
-            nb = (long long)t2 * p.tile;
+            ntile = __shfl_sync(FULL_MASK, t2, 0);
+            nkin = 0;
+            vc = (long long)ntile * cpt;
         }
-        nxt.cb = nb < n ? nb : -1;
-        PT_BEGIN(t_stage);
-        stage_chunk<BATCH>(p, sh, nxt, n, slot ^ 1, lane, wid, lim16);
-        PT_END(p.st, 0, t_stage);
+        {
+            long long ncb = -1, ncend = 0;
+            if (vc < nchunks) chunk_of<BATCH>(p, vc, ordered, n, ncb, ncend);
+            PT_BEGIN(t_stage);
+            stage_chunk<BATCH>(p, sh, ncb, ncend, ntile, nkin, slot ^ 1, lane, wid, lim16, nxt);
+            PT_END(p.st, 0, t_stage);
+        }
 
-        bool staged = cur.soff >= 0;
+        bool staged = soff >= 0;
         PT_BEGIN(t_wait);
         if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = false;
-        if (ordered && window > 0 && cur.kin == 0 && cur.tile >= window) wait_tile_done(p, cur.tile - window, lane);
+        if (ordered && window > 0 && kin == 0 && tile >= window) wait_tile_done(p, tile - window, lane);
         PT_END(p.st, 1, t_wait);
         PT_BEGIN(t_proc);
+        const int32_t v = cur.deg >= 0 ? (int32_t)(cb + lane) : -1;
+        const int64_t end = cur.beg + (cur.deg > 0 ? cur.deg : 0);
         bool sus = false;
         if (staged) {
-            const StagedEnts ent{sh.seg[wid][slot], cur.soff};
+            const StagedEnts ent{sh.seg[wid][slot], soff};
             if (ordered)
-                sus = chunk_tent_ordered(p, ent, cur.cb, cur.v, cur.beg, cur.end, cur.nbase, W, mb, sh.warp_bm[wid],
-                                         lane, in.dmax);
+                sus = chunk_tent_ordered<StagedEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
+                                                            sh.warp_bm[wid], lane, in.dmax);
             else
-                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, cur.v, cur.beg, cur.end, cur.nbase, cur.g,
-                                        R, W, push, mb, lane, wid);
+                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, v, cur.beg, end, cur.nbase, cur.g, R, W,
+                                        push, mb, lane, wid);
         } else {
             const GlobalEnts ent{p.col_idx};
             if (ordered)
-                sus = chunk_tent_ordered(p, ent, cur.cb, cur.v, cur.beg, cur.end, cur.nbase, W, mb, sh.warp_bm[wid],
-                                         lane, in.dmax);
+                sus = chunk_tent_ordered<GlobalEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
+                                                            sh.warp_bm[wid], lane, in.dmax);
             else
-                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, cur.v, cur.beg, cur.end, cur.nbase, cur.g,
-                                        R, W, push, mb, lane, wid);
+                chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, v, cur.beg, end, cur.nbase, cur.g, R, W,
+                                        push, mb, lane, wid);
         }
         // Round 0 with push: the suspects form the first repair worklist.
-        if (ordered && push) push_lanes<BATCH>(p, sus, cur.v, (int)(cur.end - cur.beg), cur.g, it, lane, false);
+        if (ordered && push) push_lanes<BATCH>(p, sus, v, cur.deg, cur.g, it, lane, false);
         PT_END(p.st, ordered ? 2 : 3, t_proc);
-        if (ordered && window > 0 && last_of_tile) publish_tile_done(p, cur.tile, lane);
+        if (ordered && window > 0 && last_of_tile) publish_tile_done(p, tile, lane);
         __syncwarp();  // every lane is done with seg[slot] before it is refilled
-        if ((threadIdx.x & 31) == 0) {
-#ifdef GC_PHASE_TIMING
-            atomicAdd(&p.st->dbg[4 + (staged ? 1 : 0)], 1ull);
-#endif
-        }
         cur = nxt;
         slot ^= 1;
     }
@@ -981,10 +1182,61 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
     }
 }
 
+// Block 0: decide which graphs are coloured in id order by one warp (round
+// 0 of the asynchronous mode), list them, and number the chunks of the other
+// graphs (prefix sums in uofs).  window 1: every graph; 0: graphs of at most
+// kOrderedSmall vertices and graphs whose sampled lower neighbours mostly lie
+// within kNearIds ids; else none.
+template <bool BATCH>
+__device__ void plan_ordering(const KParams &p, Shared &sh)
+{
+    DevState *st = p.st;
+    const int window = p.window;
+    long long carry = 0;
+    long long *warp_tot = reinterpret_cast<long long *>(sh.hub_bm);  // block-local scratch
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int g0 = 0; g0 < p.G; g0 += kBlock) {
+        const int g = g0 + threadIdx.x;
+        long long chunks = 0;
+        if (g < p.G) {
+            const long long ng = BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
+            const GraphStat gs = p.gstat[g];
+            // Small graphs are ordered too: coloured all at once they would
+            // be coloured almost simultaneously, whatever their numbering.
+            const bool ord = ng > 0 && (window == 1 || (window == 0 && (ng <= kOrderedSmall ||
+                                                                        (gs.all_lower > 0 &&
+                                                                         2 * gs.near_lower >= gs.all_lower))));
+            p.gstat[g].ordered = ord;
+            if (ord) p.olist[atomicAdd(&st->n_ordered, 1)] = g;
+            else chunks = (ng + 31) / 32;
+        }
+        // block-wide exclusive scan of chunks
+        long long x = chunks;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        long long before = carry;
+        for (int w = 0; w < wid; ++w) before += warp_tot[w];
+        if (g < p.G) p.uofs[g] = before + x - chunks;
+        long long tile_total = 0;
+        for (int w = 0; w < kWarps; ++w) tile_total += warp_tot[w];
+        __syncthreads();
+        carry += tile_total;
+    }
+    if (threadIdx.x == 0) {
+        p.uofs[p.G] = carry;
+        st->n_uchunks = carry;
+    }
+}
+
 template <bool ASYNC, bool BATCH>
 __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 {
-    __shared__ Shared sh;
+    extern __shared__ __align__(128) unsigned char gc_smem[];
+    Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
     DevState *st = p.st;
     const int lane = threadIdx.x & 31;
     const bool twop = (p.mode & GC_ALG_TWO_PHASE) != 0;
@@ -1019,6 +1271,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 row_of<BATCH>(p, v, beg, end, nbase, g);
                 hub = (end - beg) > p.t2;
                 midv = tiers && !hub && (end - beg) > p.t1;
+                if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
                 st_color<false>(p.cA + v, ASYNC ? 0 : 1);
                 if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
                 if (!ASYNC) mb += 4;
@@ -1058,26 +1311,38 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < ntiles; t += stride)
                 p.done[t] = 0;
             if (p.window == 0) {
-                unsigned long long near = 0, all = 0;
-                for (long long vi = ((long long)blockIdx.x * kBlock + threadIdx.x) * kLocalitySample; vi < p.n;
-                     vi += stride * kLocalitySample) {
-                    int64_t beg, end;
-                    int32_t nbase, g;
-                    row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, g);
-                    for (int64_t k = beg; k < end; ++k) {
-                        const int32_t u = nbase + __ldg(p.col_idx + k);
-                        if (u >= (int32_t)vi) break;
-                        ++all;
-                        near += ((int32_t)vi - u) < kNearIds;
+                // Per graph: how many sampled lower neighbours sit within
+                // kNearIds ids of their vertex.
+                for (long long b1 = (long long)blockIdx.x * kBlock * kLocalitySample; b1 < p.n;
+                     b1 += stride * kLocalitySample) {
+                    const long long vi = b1 + (long long)threadIdx.x * kLocalitySample;
+                    unsigned long long near = 0, all = 0;
+                    int32_t g = -1;
+                    if (vi < p.n) {
+                        int64_t beg, end;
+                        int32_t nbase;
+                        row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, g);
+                        for (int64_t k = beg; k < end; ++k) {
+                            const int32_t u = nbase + __ldg(p.col_idx + k);
+                            if (u >= (int32_t)vi) break;
+                            ++all;
+                            near += ((int32_t)vi - u) < kNearIds;
+                        }
                     }
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    near += __shfl_down_sync(FULL_MASK, near, o);
-                    all += __shfl_down_sync(FULL_MASK, all, o);
-                }
-                if (lane == 0 && all) {
-                    atomicAdd(&st->near_lower, near);
-                    atomicAdd(&st->all_lower, all);
+                    const int g0 = __shfl_sync(FULL_MASK, g, 0);
+                    if (__all_sync(FULL_MASK, g == g0 || g < 0)) {
+                        for (int o = 16; o > 0; o >>= 1) {
+                            near += __shfl_down_sync(FULL_MASK, near, o);
+                            all += __shfl_down_sync(FULL_MASK, all, o);
+                        }
+                        if (lane == 0 && all) {
+                            atomicAdd(&p.gstat[g0].near_lower, near);
+                            atomicAdd(&p.gstat[g0].all_lower, all);
+                        }
+                    } else if (g >= 0 && all) {
+                        atomicAdd(&p.gstat[g].near_lower, near);
+                        atomicAdd(&p.gstat[g].all_lower, all);
+                    }
                 }
             }
         }
@@ -1087,14 +1352,16 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         const int hub_all_n = ld_volatile(&st->hub_all_count);
         const int mid_all_n = ld_volatile(&st->mid_all_count);
         int q = 0;
-        int window = p.window;
-        if (ASYNC && window == 0) {
+        // Tile window for the round-0 pass over the graphs that are not
+        // coloured in id order by one warp (window > 1 only).
+        const int window = p.window > 1 ? p.window : -1;
+        if (ASYNC && alive) {
             // Ids of a naturally numbered mesh are local: neighbours would be
-            // coloured concurrently unless tiles go strictly in order.
-            const unsigned long long near = *(volatile unsigned long long *)&st->near_lower;
-            const unsigned long long all = *(volatile unsigned long long *)&st->all_lower;
-            window = (all > 0 && 2 * near >= all) ? 1 : -1;
-            if (blockIdx.x == 0 && threadIdx.x == 0) st->window = window;
+            // coloured concurrently unless the graph goes strictly in id order.
+            if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
+            grid_sync(st, nbl);
+            alive = ld_volatile(&st->error) == 0;
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
         }
 
         // Stages: one (all of V), or, with tiers, hubs -> mid degree -> low
@@ -1279,7 +1546,8 @@ __global__ void validate_kernel(KParams p)
             gn = __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g);
             lo_e = __ldg(p.edge_off + g);
             hi_e = __ldg(p.edge_off + g + 1);
-            if (v == nbase && __ldg(p.row_ptr + nbase + g) != 0) bad = true;
+            const int64_t rpo = p.rp_off ? __ldg(p.rp_off + g) : (int64_t)nbase + g;
+            if (v == nbase && __ldg(p.row_ptr + rpo) != 0) bad = true;
         }
         if (!BATCH) {
             hi_e = p.nnz;
@@ -1357,7 +1625,7 @@ static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kBlock);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = sizeof(Shared);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -1373,11 +1641,30 @@ cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cud
     return batch ? launch_one<false, true>(p, grid, s) : launch_one<false, false>(p, grid, s);
 }
 
+static const void *color_kernel_ptr(bool async, bool batch)
+{
+    return async ? (batch ? (const void *)color_kernel<true, true> : (const void *)color_kernel<true, false>)
+                 : (batch ? (const void *)color_kernel<false, true> : (const void *)color_kernel<false, false>);
+}
+
+cudaError_t prepare_color_kernels()
+{
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const cudaError_t e = cudaFuncSetAttribute(color_kernel_ptr(a, b),
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)sizeof(Shared));
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
 cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm)
 {
-    const void *f = async ? (batch ? (const void *)color_kernel<true, true> : (const void *)color_kernel<true, false>)
-                          : (batch ? (const void *)color_kernel<false, true> : (const void *)color_kernel<false, false>);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kBlock, 0);
+    const cudaError_t e = prepare_color_kernels();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, color_kernel_ptr(async, batch), kBlock,
+                                                         sizeof(Shared));
 }
 
 size_t color_smem_bytes() { return sizeof(Shared); }

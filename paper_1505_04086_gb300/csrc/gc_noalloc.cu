@@ -38,7 +38,10 @@ constexpr size_t kOffState = 0;
 constexpr size_t kOffBitmap = align256(sizeof(gc::DevState));
 constexpr size_t kOffRounds = kOffBitmap + align256(gc::kStatBitmapWords * sizeof(uint32_t));
 constexpr size_t kOffDone = kOffRounds + align256(kRoundSizes * sizeof(int32_t));
-constexpr size_t kOffB = kOffDone + align256(((size_t)kMaxN / 32 + 2) * sizeof(int32_t));
+constexpr size_t kOffGstat = kOffDone + align256(((size_t)kMaxN / 32 + 2) * sizeof(int32_t));
+constexpr size_t kOffUofs = kOffGstat + align256(sizeof(gc::GraphStat));
+constexpr size_t kOffOlist = kOffUofs + align256(2 * sizeof(int64_t));
+constexpr size_t kOffB = kOffOlist + align256(sizeof(int32_t));
 constexpr size_t kOffWl0 = kOffB + kVec;
 constexpr size_t kOffWl1 = kOffWl0 + kVec;
 constexpr size_t kOffHb0 = kOffWl1 + kVec;
@@ -158,6 +161,9 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     p.mid_all = reinterpret_cast<int32_t *>(base + kOffMidAll);
     p.hub_cap = n;
     p.done = reinterpret_cast<int32_t *>(base + kOffDone);
+    p.gstat = reinterpret_cast<gc::GraphStat *>(base + kOffGstat);
+    p.uofs = reinterpret_cast<int64_t *>(base + kOffUofs);
+    p.olist = reinterpret_cast<int32_t *>(base + kOffOlist);
     p.st = reinterpret_cast<gc::DevState *>(base + kOffState);
     p.round_sizes = reinterpret_cast<int32_t *>(base + kOffRounds);
     p.round_sizes_cap = kRoundSizes;
@@ -184,6 +190,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
 
     // Clear what must start at zero: the launch state and the colour bitmap.
     cudaError_t e = cudaMemsetAsync(p.st, 0, sizeof(gc::DevState), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.gstat, 0, sizeof(gc::GraphStat), st);
     if (e == cudaSuccess && stats)
         e = cudaMemsetAsync(base + kOffBitmap, 0, gc::kStatBitmapWords * sizeof(uint32_t), st);
     if (e == cudaSuccess && (mode & GC_VALIDATE)) e = gc::launch_validate(p, false, aux_grid, st);

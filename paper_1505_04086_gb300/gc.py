@@ -80,6 +80,15 @@ class gc_batch(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
 
 
+class gc_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("waves", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("queued", ctypes.c_int32),
+                ("resident", ctypes.c_int32), ("max_wave_graphs", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
 # Every function the header declares, with its ctypes signature.
 _P = ctypes.c_void_p
 _SIGS = {
@@ -94,6 +103,14 @@ _SIGS = {
     "gc_ctx_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
     "gc_color_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32,
                                       ctypes.POINTER(gc_opts), _P, _P, _P, _P]),
+    "gc_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
+                                        ctypes.c_uint32, ctypes.POINTER(gc_opts)]),
+    "gc_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "gc_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(gc_stats)]),
+    "gc_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(gc_stats), ctypes.c_int32]),
+    "gc_server_query": (ctypes.c_int, [_P, ctypes.POINTER(gc_server_info)]),
+    "gc_server_destroy": (None, [_P]),
     "gc_color_noalloc": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts), _P,
                                         ctypes.POINTER(gc_stats), _P]),
@@ -330,3 +347,67 @@ class Context:
         if check and rc != GC_OK:
             raise GCError(rc, "gc_ctx_stats")
         return colors_out, rounds, confl, rc, st
+
+
+class Server:
+    """Continuous-batching colouring server (gc_server_*): submit host graphs,
+    poll or wait for their colourings."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 1 << 30, max_slots: int = 4096,
+                 mode: int = 0, opts=None):
+        h = ctypes.c_void_p()
+        o = _opts(opts)
+        rc = load().gc_server_create(ctypes.byref(h), int(device), int(budget_bytes), int(max_slots),
+                                     int(mode), ctypes.byref(o) if o is not None else None)
+        if rc != GC_OK:
+            raise GCError(rc, "gc_server_create")
+        self.handle = int(h.value)
+
+    def submit(self, row_ptr: np.ndarray, col_idx: np.ndarray) -> int:
+        """Queue a graph given by host int32 arrays; returns its ticket."""
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        csr = gc_csr(rp.ctypes.data, ci.ctypes.data if ci.size else 0)
+        t = ctypes.c_uint64()
+        rc = load().gc_server_submit(ctypes.c_void_p(self.handle), ctypes.byref(csr), rp.size - 1,
+                                     ci.size, ctypes.byref(t))
+        if rc != GC_OK:
+            raise GCError(rc, "gc_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, n: int):
+        """(status, colours or None, stats); status GC_PENDING while running."""
+        col = np.empty(max(n, 1), np.int32)
+        st = gc_stats()
+        rc = load().gc_server_poll(ctypes.c_void_p(self.handle), ctypes.c_uint64(ticket), col.ctypes.data,
+                                   ctypes.byref(st))
+        if rc == GC_PENDING:
+            return rc, None, None
+        return rc, col[:n], stats_dict(st)
+
+    def wait(self, ticket: int, n: int, timeout_ms: int = -1):
+        col = np.empty(max(n, 1), np.int32)
+        st = gc_stats()
+        rc = load().gc_server_wait(ctypes.c_void_p(self.handle), ctypes.c_uint64(ticket), col.ctypes.data,
+                                   ctypes.byref(st), int(timeout_ms))
+        if rc == GC_PENDING:
+            return rc, None, None
+        return rc, col[:n], stats_dict(st)
+
+    def info(self) -> dict:
+        i = gc_server_info()
+        rc = load().gc_server_query(ctypes.c_void_p(self.handle), ctypes.byref(i))
+        if rc != GC_OK:
+            raise GCError(rc, "gc_server_query")
+        return {k: getattr(i, k) for k, _ in gc_server_info._fields_ if k != "pad"}
+
+    def close(self):
+        if self.handle:
+            load().gc_server_destroy(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

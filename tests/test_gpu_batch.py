@@ -105,3 +105,19 @@ def test_batch_validate_and_empty(ctx):
     bad.col_idx[e0] = (bad.col_idx[e0] + 1) % int(bad.vtx_off[g + 1] - bad.vtx_off[g])
     rc, *_ = run_batch(ctx, bad, gc.GC_VALIDATE)
     assert rc == gc.GC_ERR_GRAPH
+
+
+def test_async_batch_quality_per_graph(ctx):
+    # Naturally numbered meshes are coloured in id order by one warp each
+    # (sequential First-Fit exactly); random-order graphs speculatively.
+    b = I.batch(64, 1 << 9, 1 << 14, seed=21, threads=8)
+    for alg in (gc.GC_ALG_RSOC,):
+        rc, col, rounds, confl, st = run_batch(ctx, b, alg | gc.GC_SCHED_ASYNC)
+        assert rc == gc.GC_OK
+        for g in range(b.G):
+            sub = b.graph(g)
+            v0, v1 = int(b.vtx_off[g]), int(b.vtx_off[g + 1])
+            bad, mx, _ = O.check(sub, col[v0:v1])
+            assert bad == 0
+            ff = int(O.ff(sub).max())
+            assert mx <= 1.1 * ff, f"graph {g} kind {b.kind[g]}: {mx} vs first-fit {ff}"
