@@ -609,6 +609,8 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     const unsigned midmask = __ballot_sync(FULL_MASK, mid);
     unsigned long long ext = 0;
     unsigned low = 0;
+    const int32_t cb32 = (int32_t)cbase;  // ids are below 2^31
+    const int32_t v032 = (int32_t)v0;
     // Every vertex is written once in round 0, so a non-zero colour read
     // for a neighbour is that neighbour's final round-0 colour and the
     // First-Fit choice avoids it.  Lanes inside the chunk are resolved in
@@ -625,8 +627,8 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
                 u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
-                const long long d = (long long)u[q] - cbase;
-                const bool inside = u[q] >= 0 && d >= 0 && d < 32 && !((hubmask >> d) & 1u);
+                const uint32_t d = (uint32_t)(u[q] - cb32);  // in-chunk offset (wraps when outside)
+                const bool inside = u[q] >= 0 && d < 32u && !((hubmask >> d) & 1u);
                 if (inside && u[q] < v && !((midmask >> d) & 1u)) low |= 1u << d;
                 outside[q] = u[q] >= 0 && !inside;
             }
@@ -637,11 +639,11 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
                 for (int q = 0; q < kUnroll; ++q) {
                     glob[q] = outside[q];
                     c[q] = 0;
-                    if (outside[q] && u[q] < cbase && u[q] >= v0 && cbase - u[q] <= kRingIds) {
+                    if (outside[q] && u[q] < cb32 && u[q] >= v032 && cb32 - u[q] <= kRingIds) {
                         const uint16_t r = ring[u[q] & (kRingIds - 1)];
                         glob[q] = r == kRingGlobal;
                         c[q] = r;
-                    } else if (outside[q] && skip_higher && u[q] >= cbase + 32) {
+                    } else if (outside[q] && skip_higher && u[q] >= cb32 + 32) {
                         glob[q] = false;  // not coloured yet in id order
                     }
                 }
@@ -665,18 +667,36 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     PT_BEGIN(t_r);
     int mine = thr ? __ffsll((long long)~ext) : 0;
     // In-chunk dependencies: walk only the lanes between the first lane some
-    // lane depends on and the last dependent lane, in id order.
+    // lane depends on and the last dependent lane, in id order.  Branch-free:
+    // every lane recomputes its candidate each step and lane k's is taken.
     const unsigned dependent = __ballot_sync(FULL_MASK, low != 0u);
     if (dependent) {
         const unsigned needed = __reduce_or_sync(FULL_MASK, low);
         const int k0 = __ffs(needed) - 1;
         const int k1 = 31 - __clz(dependent);
-        for (int k = k0; k <= k1; ++k) {
-            if (lane == k && thr) mine = __ffsll((long long)~ext);
-            const int ck = __shfl_sync(FULL_MASK, mine, k);
-            if ((low >> k) & 1u) ext |= 1ull << (ck - 1);
+        // 32-bit masks suffice when every lane keeps a free colour in 1..31
+        // whatever its in-chunk neighbours pick.
+        const bool narrow = __all_sync(FULL_MASK, (ext >> 31) == 0ull &&
+                                                      __popc((uint32_t)ext) + __popc(low) <= 30);
+        if (narrow) {
+            uint32_t e32 = (uint32_t)ext;
+            for (int k = k0; k <= k1; ++k) {
+                const int cand = __ffs(~e32);
+                const int ck = __shfl_sync(FULL_MASK, cand, k);
+                mine = (lane == k) ? cand : mine;
+                e32 |= ((low >> k) & 1u) << (ck - 1);
+            }
+            if (lane > k1) mine = __ffs(~e32);
+        } else {
+            for (int k = k0; k <= k1; ++k) {
+                const int cand = __ffsll((long long)~ext);
+                const int ck = __shfl_sync(FULL_MASK, cand, k);
+                mine = (lane == k) ? cand : mine;
+                ext |= (unsigned long long)((low >> k) & 1u) << (ck - 1);
+            }
+            if (lane > k1) mine = __ffsll((long long)~ext);
         }
-        if (thr && lane > k1) mine = __ffsll((long long)~ext);
+        if (!thr) mine = 0;
     }
     PT_END(p.st, 7, t_r);
     if (thr) {
