@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--mode", default="rsoc_async", help="batch/serve workloads: colouring mode")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline mode only")
     return ap.parse_args()
@@ -155,6 +156,7 @@ class ClockSampler:
 
 MODES = {
     "rsoc_async": 0 | 2,        # GC_ALG_RSOC | GC_SCHED_ASYNC (headline)
+    "rsoc_async_keepers": 0 | 2 | 512,  # ... | GC_FF_KEEPERS
     "rsoc_det": 0,              # GC_ALG_RSOC | GC_SCHED_DET
     "twophase_async": 1 | 2,    # GC_ALG_TWO_PHASE | GC_SCHED_ASYNC
     "twophase_det": 1,
@@ -397,8 +399,11 @@ BATCH_G = 4096
 
 
 def run_batch(args, ws, rank, local):
-    """Many uneven graphs in one persistent launch (gc_color_batch) against
-    one plain launch per graph.  Every rank colours its own share of the
+    """Many uneven graphs in one persistent launch, against one plain launch
+    per graph.  The options (bin thresholds, tile, blocks per SM, tail,
+    ordering) come from the library's autotuner, run on the batch before the
+    timed region; each timed step replays the batch colouring captured in a
+    CUDA graph (gc_plan_launch).  Every rank colours its own share of the
     graphs (sharded by size, no collective)."""
     import torch
     from paper_1505_04086_gb300 import gc
@@ -424,33 +429,46 @@ def run_batch(args, ws, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = gc.Context(local)
-    mode = MODES["rsoc_async"]
+    mode_name = args.mode
+    mode = MODES[mode_name]
     steps = max(3, min(args.steps, 20))
-    for _ in range(args.warmup):
-        assert gc.gc_color_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, rounds, confl,
-                                 None, stream) == gc.GC_OK
-        assert gc.gc_ctx_stats(ctx.handle)[0] == gc.GC_OK
+    t_tune = time.perf_counter()
+    rc, tune = gc.gc_autotune_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, reps=1)
+    if rc != gc.GC_OK:
+        raise RuntimeError(gc.gc_strerror(rc))
+    t_tune = time.perf_counter() - t_tune
+    opts = tune["best"]
+    plan = gc.Plan(local, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, rounds, confl, opts=opts)
+    for _ in range(max(3, args.warmup)):
+        assert plan.launch(stream) == gc.GC_OK
+        assert plan.stats()[0] == gc.GC_OK
     sampler = ClockSampler(local)
     sampler.start()
-    ms, kms = [], []
+    ms, kms, mbs = [], [], []
     for _ in range(steps):
         flush.zero_()
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        rc = gc.gc_color_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, rounds, confl,
-                               None, stream)
+        rc = plan.launch(stream)
         z.record(stream)
-        rc2, st = gc.gc_ctx_stats(ctx.handle)
+        rc2, st = plan.stats()
         if rc != gc.GC_OK or rc2 != gc.GC_OK:
             raise RuntimeError(gc.gc_strerror(rc2))
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(z))
         kms.append(st["elapsed_ms"])
+        mbs.append(st["model_bytes"])
     clocks = sampler.stop()
     units, secs = D.aggregate(steps * E, sum(ms) / 1e3, device=dev)
     gunits, _ = D.aggregate(steps * G, 0.0, device=dev)
     peak, peak_kind = measured_peak()
-    achieved = st["model_bytes"] / (np.mean(kms) / 1e3) / 1e9
+    achieved = float(np.mean(mbs)) / (np.mean(kms) / 1e3) / 1e9
+    # validity of every graph's colouring, checked on the device (untimed)
+    rc = gc.gc_color_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode | gc.GC_CHECKED, col,
+                           None, None, opts, stream)
+    rc2, _ = gc.gc_ctx_stats(ctx.handle)
+    if rc != gc.GC_OK or rc2 != gc.GC_OK:
+        raise RuntimeError(f"device check of the batch colouring failed: {gc.gc_strerror(rc2)}")
     # per-graph plain launches, same graphs, same mode (one pass)
     subs = []
     for g in range(G):
@@ -470,16 +488,22 @@ def run_batch(args, ws, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded generator)",
             "config": {"workload": f"batch{BATCH_G}_mesh_rgg_1k_256k", "graphs": BATCH_G,
-                       "n": int(full.total_n), "edges": int(full.total_nnz // 2), "mode": "rsoc_async",
-                       "l2": "flushed between steps (512 MB write)", "parallelism": f"graph-shards{ws}"},
+                       "n": int(full.total_n), "edges": int(full.total_nnz // 2), "mode": mode_name,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"graph-shards{ws}",
+                       "launch": "CUDA graph replay (gc_plan_launch)"},
             "graphs_per_s": round(gunits / secs, 1),
+            "p50_ms": round(pct(ms, 50), 4), "p99_ms": round(pct(ms, 99), 4),
             "plain_launches_graphs_per_s": round(ws * G / plain_s, 1),
             "speedup_vs_plain": round((gunits / secs) / (ws * G / plain_s), 2),
+            "autotune": {"opts": opts, "best_ms": round(tune["best_ms"], 3),
+                         "default_ms": round(tune["default_ms"], 3), "evaluated": tune["evaluated"],
+                         "seconds": round(t_tune, 1)},
             "rounds": st["rounds"], "conflicts": st["conflicts"],
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
                          "traffic": None, "kernel": "gc::color_kernel<async,batch>"},
-            "gpu_launches": 2 * steps, "clocks": clocks}
+            "gpu_launches": 4 * steps, "clocks": clocks}  # lut, colour, stats, popcount
+    plan.close()
     ctx.close()
     if ws > 1:
         import torch.distributed as dist
@@ -510,7 +534,7 @@ def run_serve(args, ws, rank, local):
     picks = [(rm[int(rng.integers(len(rm)))] if rng.random() < 0.05 else pool[int(rng.integers(len(pool)))])
              for _ in range(nreq)]
     budget = 8 << 30
-    mode = MODES["rsoc_async"]
+    mode = MODES[args.mode]
 
     def serve(rate):
         srv = gc.Server(local, budget_bytes=budget, max_slots=1024, mode=mode)
@@ -577,7 +601,7 @@ def run_serve(args, ws, rank, local):
             "warmup": 0, "ms_per_step": round(1e3 / sat, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generator)",
             "config": {"workload": "serve_poisson_mix_rmat18", "requests": nreq, "budget_bytes": budget,
-                       "mode": "rsoc_async", "pool": f"{len(pool)} mix graphs + {len(rm)} rmat18"},
+                       "mode": args.mode, "pool": f"{len(pool)} mix graphs + {len(rm)} rmat18"},
             "plain_launches_graphs_per_s": round(plain_sat, 1),
             "speedup_vs_plain": round(sat / plain_sat, 2),
             "load_levels": levels,

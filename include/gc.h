@@ -80,13 +80,31 @@ enum {
                                     runs in place, every later round reads the
                                     colours of the end of the round before
                                     (fewer colours on dense cores, more rounds) */
-    GC_TIERS = 256               /* with GC_SCHED_ASYNC and GC_ALG_RSOC: colour
+    GC_TIERS = 256,              /* with GC_SCHED_ASYNC and GC_ALG_RSOC: colour
                                     the vertices of degree > t2, then those of
                                     degree > t1, then the rest, each tier taken
                                     through round 0 and its repair rounds before
                                     the next (later tiers are uncoloured while
                                     an earlier one is repaired) */
+    GC_FF_KEEPERS = 512          /* with GC_SCHED_ASYNC, GC_ALG_RSOC and
+                                    GC_TIE_LOWER_KEEPS only (else GC_ERR_ARG;
+                                    not with GC_REPAIR_SNAPSHOT): a vertex's
+                                    First-Fit choice, in round 0 and in every
+                                    repair, avoids only the colours of its lower
+                                    neighbours (those that keep their colour on
+                                    a tie), as sequential First-Fit in id order
+                                    sees them; a higher neighbour that then
+                                    holds the chosen colour joins the next
+                                    round's worklist.  Not the recolouring step
+                                    of Algorithm 3 (which avoids every
+                                    neighbour): colour counts stay close to
+                                    sequential First-Fit under heavy
+                                    concurrency.  conflicts counts those
+                                    handed-on neighbours too. */
 };
+
+/* Every mode bit above. */
+#define GC_MODE_MASK 1023u
 
 /* ---- device error word bits (gc_stats.error_word) ---------------------- */
 enum {
@@ -241,6 +259,56 @@ typedef struct {
 int gc_color_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, const gc_opts *opts,
                    int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out,
                    void *stream);
+
+/* ---- batch plans: one batch colouring captured in a CUDA graph ---------- */
+
+typedef struct gc_plan gc_plan;
+
+/*
+ * Capture one gc_color_batch call (its memsets, kernels, event records and
+ * statistics read-back) into a CUDA graph on `device`, to be replayed by
+ * gc_plan_launch with no host-side planning or allocation per launch.  The
+ * plan owns a private context whose scratch memory is sized here and never
+ * moves.  Every launch colours the same arrays: the batch's device arrays,
+ * colors_out and the optional rounds_out/conflicts_out must stay allocated
+ * and in place until gc_plan_destroy.  Returns GC_ERR_CUDA if the device
+ * cannot capture the launch.
+ */
+int gc_plan_create(const gc_batch *batch, int device, uint32_t mode, const gc_opts *opts,
+                   int32_t *colors_out, int32_t *rounds_out, int64_t *conflicts_out, gc_plan **plan);
+
+/* Replay the captured colouring on `stream` (asynchronous). */
+int gc_plan_launch(gc_plan *plan, void *stream);
+
+/* Wait for the last launch and report it (as gc_ctx_stats). */
+int gc_plan_stats(gc_plan *plan, gc_stats *stats);
+
+/* Wait for the last launch and free the plan. */
+void gc_plan_destroy(gc_plan *plan);
+
+/* ---- autotuning the options of a batch ---------------------------------- */
+
+typedef struct {
+    gc_opts best;                /* fastest option set found */
+    float best_ms;               /* its median device time */
+    float default_ms;            /* median device time with default options */
+    int32_t evaluated;           /* option sets timed */
+} gc_tune_result;
+
+/*
+ * Choose gc_opts for colouring this batch in `mode` by timing it: coordinate
+ * descent from the defaults over t1 (largest degree coloured by one
+ * thread), t2 (largest degree coloured by one warp; above it a block per
+ * vertex), tile, blocks_per_sm, tail and, for GC_SCHED_ASYNC, window; each
+ * candidate's cost is the median of `reps` (1..64) runs' device time
+ * (CUDA events), and at most two sweeps are made.  Synchronous (legacy
+ * default stream); colors_out (device, total_n entries) receives the
+ * colourings while it runs.  In GC_SCHED_DET mode every option set gives
+ * the same colouring, so only speed is at stake.  Returns the first error
+ * of any run.
+ */
+int gc_autotune_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, int32_t reps, int32_t *colors_out,
+                      gc_tune_result *result);
 
 /* ---- serving: continuous batching of colouring requests ------------------ */
 

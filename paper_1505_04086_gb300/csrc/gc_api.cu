@@ -11,62 +11,13 @@
 #include <unordered_map>
 
 #include "gc.h"
+#include "gc_ctx.h"
 #include "gc_internal.h"
 
+using gc::Buf;
 using gc::DevState;
 using gc::KParams;
-
-namespace {
-
-constexpr int kRoundSizesDev = 65536;  // per-iteration |L| kept on the device
-
-struct Buf {
-    void *p = nullptr;
-    size_t bytes = 0;
-    // Grow-only device buffer.  Returns false on allocation failure.
-    bool reserve(size_t need)
-    {
-        if (need <= bytes) return true;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        if (cudaMalloc(&p, need) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        bytes = need;
-        return true;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <class T> T *as() const { return static_cast<T *>(p); }
-};
-
-}  // namespace
-
-struct gc_ctx {
-    int device = 0;
-    int num_sms = 0;
-    int occ[2][2] = {{0, 0}, {0, 0}};
-    // scratch
-    Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done, gstat, uofs, olist;
-    Buf stage_rp, stage_ci, stage_col;  // gc_color host staging
-    DevState *st_host = nullptr;        // pinned
-    int32_t *rs_host = nullptr;         // pinned round sizes
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
-    // last enqueued call
-    bool pending = false;
-    int launch_status = GC_OK;
-    int32_t last_n = 0;
-    uint32_t last_mode = 0;
-    bool last_empty = false;
-    bool last_stats = false;
-    int32_t last_rounds_copied = 0;
-};
+using gc::kRoundSizesDev;
 
 namespace {
 
@@ -144,6 +95,13 @@ int grid_for(gc_ctx *c, bool async, bool batch, const Resolved &r, int64_t n)
     return (int)grid;
 }
 
+// Event record on s; while a CUDA graph is being captured the record
+// becomes a node of the graph, so timing and completion work on replays.
+cudaError_t record(gc_ctx *c, cudaEvent_t ev, cudaStream_t s)
+{
+    return c->capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+}
+
 // Enqueue the colouring described by p (single graph or batch) on s.
 int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r, cudaStream_t s)
 {
@@ -169,6 +127,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.uofs = c->uofs.as<int64_t>();
     p.olist = c->olist.as<int32_t>();
     p.cB = c->cB.as<int32_t>();
+    p.mark = (mode & GC_FF_KEEPERS) ? p.cB : nullptr;
     p.wl[0] = c->wl0.as<int32_t>();
     p.wl[1] = c->wl1.as<int32_t>();
     p.hub[0] = c->hb0.as<int32_t>();
@@ -188,21 +147,21 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     if ((mode & GC_VALIDATE) && (e = gc::launch_validate(p, batch, aux_grid, s)) != cudaSuccess)
         return cuda_status(e);
     const int grid = grid_for(c, async, batch, r, n);
-    if ((e = cudaEventRecord(c->ev0, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = record(c, c->ev0, s)) != cudaSuccess) return cuda_status(e);
     if ((e = gc::launch_color(p, async, batch, grid, s)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaEventRecord(c->ev1, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = record(c, c->ev1, s)) != cudaSuccess) return cuda_status(e);
     if ((mode & GC_CHECKED) && (e = gc::launch_check(p, batch, aux_grid, s)) != cudaSuccess)
         return cuda_status(e);
     if (stats && (e = gc::launch_color_stats(p.cA, p.n, p.st, c->bitmap.as<uint32_t>(), aux_grid, s)) != cudaSuccess)
         return cuda_status(e);
     if ((e = cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_status(e);
-    c->last_rounds_copied = 256;
+    c->last.rounds_copied = 256;
     if ((e = cudaMemcpyAsync(c->rs_host, c->round_sizes.p, 256 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
         cudaSuccess)
         return cuda_status(e);
-    if ((e = cudaEventRecord(c->ev_done, s)) != cudaSuccess) return cuda_status(e);
-    c->last_stats = stats;
+    if ((e = record(c, c->ev_done, s)) != cudaSuccess) return cuda_status(e);
+    c->last.stats = stats;
     return GC_OK;
 }
 
@@ -238,22 +197,30 @@ gc_ctx *default_ctx()
 
 namespace gc {
 
+int reserve_batch(gc_ctx *c, int32_t G, int64_t total_n, uint32_t mode)
+{
+    const int64_t lut_entries = (total_n + (1 << kLutShift) - 1) >> kLutShift;
+    int rc = ensure_scratch(c, total_n, needs_second_buffer(mode), true, lut_entries);
+    if (rc == GC_OK) rc = ensure_graph_tables(c, G);
+    return rc;
+}
+
 int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, const int64_t *vtx_off,
                      const int64_t *edge_off, const int64_t *rp_off, const int32_t *row_ptr, const int32_t *col_idx,
                      uint32_t mode, const gc_opts *opts, int32_t *colors_out, int32_t *rounds_out,
                      int64_t *conflicts_out, cudaStream_t s)
 {
-    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
+    if (!gc::mode_ok(mode)) return GC_ERR_ARG;
     if (total_n > 0 && !colors_out) return GC_ERR_ARG;
     Resolved r;
     // The cap applies per graph; every graph's own bound is below total_n + 1.
     int rc = resolve_opts(opts, total_n, r);
     if (rc != GC_OK) return rc;
-    c->pending = false;
-    c->last_n = (int32_t)total_n;
-    c->last_mode = mode;
-    c->last_empty = (total_n == 0);
-    c->launch_status = GC_OK;
+    c->last.pending = false;
+    c->last.n = (int32_t)total_n;
+    c->last.mode = mode;
+    c->last.empty = (total_n == 0);
+    c->last.launch_status = GC_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return GC_ERR_CUDA;
     if (G > 0 && rounds_out) {
         cudaError_t e = cudaMemsetAsync(rounds_out, 0, (size_t)G * sizeof(int32_t), s);
@@ -264,15 +231,11 @@ int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, c
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (total_n == 0) {
-        c->pending = true;
+        c->last.pending = true;
         return GC_OK;
     }
-    const bool async = (mode & GC_SCHED_ASYNC) != 0;
     const int64_t n = total_n;
-    const int64_t lut_entries = (n + (1 << kLutShift) - 1) >> kLutShift;
-    const bool need_b = !async || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE));
-    if ((rc = ensure_scratch(c, n, need_b, true, lut_entries)) != GC_OK) return rc;
-    if ((rc = ensure_graph_tables(c, G)) != GC_OK) return rc;
+    if ((rc = reserve_batch(c, G, n, mode)) != GC_OK) return rc;
     KParams p;
     memset(&p, 0, sizeof p);
     p.row_ptr = row_ptr;
@@ -288,8 +251,8 @@ int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, c
     p.g_rounds = rounds_out;
     p.g_conflicts = reinterpret_cast<unsigned long long *>(conflicts_out);
     rc = enqueue(c, p, true, mode, r, s);
-    if (rc == GC_OK) c->pending = true;
-    c->launch_status = rc;
+    if (rc == GC_OK) c->last.pending = true;
+    c->last.launch_status = rc;
     return rc;
 }
 
@@ -398,24 +361,23 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
                    int32_t *colors_out, void *stream)
 {
     if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
-    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
+    if (!gc::mode_ok(mode)) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
     Resolved r;
     int rc = resolve_opts(opts, n, r);
     if (rc != GC_OK) return rc;
-    c->pending = false;
-    c->last_n = n;
-    c->last_mode = mode;
-    c->last_empty = (n == 0);
-    c->launch_status = GC_OK;
+    c->last.pending = false;
+    c->last.n = n;
+    c->last.mode = mode;
+    c->last.empty = (n == 0);
+    c->last.launch_status = GC_OK;
     if (n == 0) {
-        c->pending = true;
+        c->last.pending = true;
         return GC_OK;
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return GC_ERR_CUDA;
-    const bool async = (mode & GC_SCHED_ASYNC) != 0;
-    const bool need_b = !async || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE));
+    const bool need_b = gc::needs_second_buffer(mode);
     if ((rc = ensure_scratch(c, n, need_b, false, 0)) != GC_OK) return rc;
     if ((rc = ensure_graph_tables(c, 1)) != GC_OK) return rc;
     KParams p;
@@ -427,21 +389,21 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
     p.nnz = nnz;
     p.cA = colors_out;
     rc = enqueue(c, p, false, mode, r, (cudaStream_t)stream);
-    if (rc == GC_OK) c->pending = true;
-    c->launch_status = rc;
+    if (rc == GC_OK) c->last.pending = true;
+    c->last.launch_status = rc;
     return rc;
 }
 
 int gc_ctx_stats(gc_ctx *c, gc_stats *out)
 {
     if (!c) return GC_ERR_ARG;
-    if (!c->pending) return c->launch_status != GC_OK ? c->launch_status : GC_ERR_ARG;
+    if (!c->last.pending) return c->last.launch_status != GC_OK ? c->last.launch_status : GC_ERR_ARG;
     gc_stats s;
     memset(&s, 0, sizeof s);
     s.colors = -1;
     s.distinct_colors = -1;
     int status = GC_OK;
-    if (c->last_empty) {
+    if (c->last.empty) {
         s.colors = 0;
         s.distinct_colors = 0;
     } else {
@@ -452,7 +414,7 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
         s.conflicts = (int64_t)d.conflicts;
         s.model_bytes = (int64_t)d.model_bytes;
         s.error_word = d.error;
-        if (c->last_stats) {
+        if (c->last.stats) {
             s.colors = d.max_color;
             s.distinct_colors = d.distinct;
         }
@@ -466,7 +428,7 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
         int32_t cap = out->round_sizes_cap;
         if (rs && cap > 0) {
             int32_t k = std::min<int32_t>(std::min<int32_t>(s.rounds, cap), kRoundSizesDev);
-            if (k > c->last_rounds_copied) {
+            if (k > c->last.rounds_copied) {
                 // more than the prefetched prefix: fetch synchronously
                 if (cudaMemcpy(c->rs_host, c->round_sizes.p, (size_t)k * sizeof(int32_t),
                                cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -484,7 +446,7 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
             const DevState &d = *c->st_host;
             const int k = std::min<int>(std::min<int>(s.rounds + 1, s.round_ns_cap), gc::kStamps);
             for (int i = 0; i < k; ++i)
-                s.round_ns[i] = (c->last_empty || d.stamp[i] == 0) ? 0 : (int64_t)(d.stamp[i] - d.t_start);
+                s.round_ns[i] = (c->last.empty || d.stamp[i] == 0) ? 0 : (int64_t)(d.stamp[i] - d.t_start);
         }
         *out = s;
     }

@@ -26,11 +26,31 @@ constexpr int kStatBitmapWords = 1 << 15;  // distinct-colour bitmap: colours < 
 constexpr int kStamps = 256;            // per-iteration end times kept in DevState
 constexpr int kWorkBits = 33;           // pushed-degree sum field of wl_packed (< 2^33 entries)
 constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
-constexpr int kNearIds = 2048;
-constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)          // locality: "near" lower neighbour id distance
+constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
+constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
+
+// Mode bits a call accepts: GC_FF_KEEPERS only with asynchronous RSOC,
+// lower-keeps ties and in-place repairs.
+inline bool mode_ok(uint32_t mode)
+{
+    if (mode & ~GC_MODE_MASK) return false;
+    if ((mode & GC_FF_KEEPERS) &&
+        (!(mode & GC_SCHED_ASYNC) ||
+         (mode & (GC_ALG_TWO_PHASE | GC_TIE_HIGHER_KEEPS | GC_REPAIR_SNAPSHOT | GC_DEBUG_NO_TIEBREAK))))
+        return false;
+    return true;
+}
+
+// The second n-entry buffer holds colours (deterministic mode, snapshot
+// repairs) or, with GC_FF_KEEPERS, the round a vertex was last queued for.
+inline bool needs_second_buffer(uint32_t mode)
+{
+    return !(mode & GC_SCHED_ASYNC) || ((mode & GC_REPAIR_SNAPSHOT) && !(mode & GC_ALG_TWO_PHASE)) ||
+           (mode & GC_FF_KEEPERS);
+}
 enum Tie : int { TIE_LOWER = 0, TIE_HIGHER = 1, TIE_NONE = 2 };
 
 // Per-graph state of one launch (a single graph is graph 0).  Zeroed
@@ -106,6 +126,7 @@ struct KParams {
     GraphStat *gstat;          // G entries (1 for a single graph)
     int64_t *uofs;             // G+1: prefix sums of the unordered graphs' chunk counts
     int32_t *olist;            // G: the ordered graphs
+    int32_t *mark;             // GC_FF_KEEPERS: n entries, last iteration a vertex was queued in + 1
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

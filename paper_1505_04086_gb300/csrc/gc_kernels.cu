@@ -229,6 +229,9 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
+#ifndef GC_KEEPERS_MIN_DEG
+#define GC_KEEPERS_MIN_DEG 0  // GC_FF_KEEPERS applies to vertices of higher degree
+#endif
 #ifndef GC_PASS_INLINE
 #define GC_PASS_INLINE __forceinline__
 #endif
@@ -245,26 +248,106 @@ struct StagedEnts {
     __device__ __forceinline__ int32_t operator()(int64_t k) const { return buf[k - off]; }
 };
 
-// Smallest colour >= 1 not held by any neighbour (Algorithm 1 body).  With
-// deg <= 62 the answer is <= 63, so a 64-bit mask of colours 1..64 suffices.
+// Smallest colour >= 1 not held by a neighbour u <= vmax (Algorithm 1 body;
+// vmax = INT32_MAX takes every neighbour, v - 1 only the lower ones, and the
+// sorted row is then read up to v).  With deg <= 62 the answer is <= 63, so
+// a 64-bit mask of colours 1..64 suffices.  t = entries read.
 template <bool ASYNC, class E>
-__device__ __forceinline__ int ff_thread(const E &ent, int64_t beg, int deg, int32_t nbase, const int32_t *R)
+__device__ __forceinline__ int ff_thread(const E &ent, int64_t beg, int deg, int32_t nbase, const int32_t *R,
+                                         int32_t vmax, int &t)
 {
     unsigned long long mask = 0;
+    t = 0;
     for (int i = 0; i < deg; i += kUnroll) {
         int u[kUnroll];
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q) u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
-        int c[kUnroll];
-#pragma unroll
-        for (int q = 0; q < kUnroll; ++q) c[q] = (u[q] >= 0) ? ld_color<ASYNC>(R + u[q]) : 0;
+        bool take[kUnroll];
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) {
+            const bool in = i + q < deg;
+            u[q] = in ? nbase + ent(beg + i + q) : 0;
+            take[q] = in && u[q] <= vmax;
+        }
+        int c[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) c[q] = take[q] ? ld_color<ASYNC>(R + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            t += take[q];
             unsigned b = (unsigned)(c[q] - 1);
             if (b < 64u) mask |= 1ull << b;
         }
+        if (!take[kUnroll - 1]) break;  // row ended, or passed vmax
     }
     return __ffsll((long long)~mask);
+}
+
+template <bool BATCH>
+__device__ __forceinline__ void note_push_graph(const KParams &p, int32_t g, int it)
+{
+    if (BATCH) {
+        if (p.g_conflicts) atomicAdd(p.g_conflicts + g, 1ull);
+        if (p.g_rounds) atomicMax(p.g_rounds + g, it + 1);
+    }
+}
+
+// GC_FF_KEEPERS: claim w for the worklist of iteration `it` (mark[w] holds
+// the last iteration w was queued in, plus one).  False: already queued.
+__device__ __forceinline__ bool claim_push(const KParams &p, int32_t w, int it)
+{
+    return atomicExch(p.mark + w, it + 1) != it + 1;
+}
+
+// GC_FF_KEEPERS: queue w (a higher neighbour that now holds the colour a
+// lower neighbour just took) for the next round, in the hub or tile list by
+// its degree.
+template <bool BATCH>
+__device__ __noinline__ void push_one(const KParams &p, int32_t w, int it)
+{
+    if (!claim_push(p, w, it)) return;
+    int64_t beg, end;
+    int32_t nbase, g;
+    row_of<BATCH>(p, w, beg, end, nbase, g);
+    const unsigned long long deg = (unsigned long long)(end - beg);
+    DevState *st = p.st;
+    if (deg > (unsigned long long)p.t2) {
+        atomicAdd(&st->wl_packed[it & (kRing - 1)], deg);
+        const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
+        if (idx < p.hub_cap) __stcg(p.hub[it & 1] + idx, w);
+        else atomicOr(&st->error, GC_EW_OVERFLOW);
+    } else {
+        const int o =
+            (int)(atomicAdd(&st->wl_packed[it & (kRing - 1)], (1ull << kWorkBits) + deg) >> kWorkBits);
+        if (o < p.n) __stcg(p.wl[it & 1] + o, w);
+        else atomicOr(&st->error, GC_EW_OVERFLOW);
+    }
+    note_push_graph<BATCH>(p, g, it);
+}
+
+// GC_FF_KEEPERS: v (lower-keeps ties) just took colour k; every higher
+// neighbour holding k now loses the tie to v and is queued.  Reads the part
+// of the sorted row above v, from its end.
+template <bool ASYNC, bool BATCH, class E>
+__device__ __forceinline__ void push_clashes_thread(const KParams &p, const E &ent, int32_t v, int64_t beg,
+                                                    int64_t end, int32_t nbase, const int32_t *R, int k, int it)
+{
+    const int deg = (int)(end - beg);
+    for (int i = 0; i < deg; i += kUnroll) {
+        int u[kUnroll];
+        bool side[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) {
+            const bool in = i + q < deg;
+            u[q] = in ? nbase + ent(end - 1 - (i + q)) : 0;
+            side[q] = in && u[q] > v;
+        }
+        int c[kUnroll];
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < kUnroll; ++q)
+            if (side[q] && c[q] == k) push_one<BATCH>(p, u[q], it);
+        if (!side[kUnroll - 1]) break;
+    }
 }
 
 // Is some neighbour on v's tie side coloured cv?  t = tie-side entries seen
@@ -304,21 +387,23 @@ __device__ __forceinline__ bool detect_thread(const E &ent, int tie, int32_t v, 
 
 // One vertex, one thread.  Returns true if v must join the next worklist.
 // Byte model accounting goes to mb (see gc.h, gc_stats.model_bytes).
-template <bool ASYNC, class E>
+template <bool ASYNC, bool BATCH, class E>
 __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, int op, int32_t v, int64_t beg,
                                               int64_t end, int32_t nbase, const int32_t *R, int32_t *W,
-                                              bool implicit, long long &mb)
+                                              bool implicit, long long &mb, int it)
 {
     const int deg = (int)(end - beg);
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const int32_t vmax = keep ? v - 1 : INT32_MAX;
     mb += (implicit ? 0 : 4) + 8;
+    int t;
     if (op == OP_TENT) {
-        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R));
-        mb += 8ll * deg + 4;
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R, vmax, t));
+        mb += 8ll * t + 4;
         return false;
     }
     const int cv = ld_color<ASYNC>(R + v);
     mb += 4;
-    int t;
     const bool d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t);
     if (op == OP_DETECT) {
         if (!ASYNC) st_color<false>(p.cA + v, cv);  // two-phase: bring buffer A up to date
@@ -326,7 +411,10 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
         return d;
     }
     if (d) {
-        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R));
+        int tf;
+        const int k = ff_thread<ASYNC>(ent, beg, deg, nbase, R, vmax, tf);
+        st_color<ASYNC>(W + v, k);
+        if (keep) push_clashes_thread<ASYNC, BATCH>(p, ent, v, beg, end, nbase, R, k, it);
         mb += 8ll * deg + 8;
     } else {
         if (W != R) st_color<ASYNC>(W + v, cv);  // snapshot rounds: carry the colour over
@@ -339,25 +427,34 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
 // warp per vertex (t1 < deg <= t2 <= kT2Max)
 // ------------------------------------------------------------------------
 
+// Warp-wide First-Fit over the neighbours u <= vmax (see ff_thread);
+// t_total = entries read.
 template <bool ASYNC>
-__device__ int ff_warp(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R,
-                       uint32_t *bm, int lane)
+__device__ int ff_warp(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R, int32_t vmax,
+                       uint32_t *bm, int lane, int &t_total)
 {
+    int t = 0;
     const int nwords = (deg + 1) / 32 + 1;  // bits for colours 0..deg+1
     __syncwarp();
     for (int w = lane; w < nwords; w += 32) bm[w] = (w == 0) ? 1u : 0u;  // colour 0 is not a colour
     __syncwarp();
     for (int i0 = 0; i0 < deg; i0 += 32 * 4) {
         int c[4];
+        bool take[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int i = i0 + q * 32 + lane;
-            c[q] = (i < deg) ? ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i)) : 0;
+            const int32_t u = (i < deg) ? nbase + __ldg(p.col_idx + beg + i) : 0;
+            take[q] = i < deg && u <= vmax;
+            c[q] = take[q] ? ld_color<ASYNC>(R + u) : 0;
+            t += take[q];
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if ((unsigned)c[q] <= (unsigned)(deg + 1)) atomicOr(&bm[c[q] >> 5], 1u << (c[q] & 31));
+        if (!(__ballot_sync(FULL_MASK, take[3]) >> 31)) break;  // row ended, or passed vmax
     }
+    t_total = __reduce_add_sync(FULL_MASK, t);
     __syncwarp();
     for (int w0 = 0; w0 < nwords; w0 += 32) {
         const int w = w0 + lane;
@@ -370,6 +467,31 @@ __device__ int ff_warp(const KParams &p, int64_t beg, int deg, int32_t nbase, co
         }
     }
     return deg + 1;  // not reached: one of 1..deg+1 is always free
+}
+
+// Warp-wide push_clashes_thread: queue v's higher neighbours that hold k.
+template <bool ASYNC, bool BATCH>
+__device__ void push_clashes_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                                  const int32_t *R, int k, int it, int lane)
+{
+    const int deg = (int)(end - beg);
+    for (int i0 = 0; i0 < deg; i0 += 32 * 4) {
+        int32_t u[4];
+        bool side[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * 32 + lane;
+            u[q] = (i < deg) ? nbase + __ldg(p.col_idx + end - 1 - i) : 0;
+            side[q] = i < deg && u[q] > v;
+        }
+        int c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (side[q] && c[q] == k) push_one<BATCH>(p, u[q], it);
+        if (!(__ballot_sync(FULL_MASK, side[3]) >> 31)) break;
+    }
 }
 
 constexpr int kWarpUnroll = 4;   // entries per lane in flight (warp path)
@@ -412,18 +534,21 @@ __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t en
     return __any_sync(FULL_MASK, def);
 }
 
-template <bool ASYNC>
+template <bool ASYNC, bool BATCH>
 __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
                             const int32_t *R, int32_t *W, bool implicit, long long &mb, uint32_t *bm,
-                            int lane)
+                            int lane, int it)
 {
     const int deg = (int)(end - beg);
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
+    int tf;
     if (op == OP_TENT) {
-        const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, bm, lane);
+        const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, vmax, bm, lane, tf);
         if (lane == 0) st_color<ASYNC>(W + v, c);
-        add += 8ll * deg + 4;
+        add += 8ll * tf + 4;
     } else {
         const int cv = ld_color<ASYNC>(R + v);
         add += 4;
@@ -433,8 +558,9 @@ __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, in
             if (!ASYNC && lane == 0) st_color<false>(p.cA + v, cv);
             add += 8ll * t + (d ? 4 : 0);
         } else if (d) {
-            const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, bm, lane);
+            const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, vmax, bm, lane, tf);
             if (lane == 0) st_color<ASYNC>(W + v, c);
+            if (keep) push_clashes_warp<ASYNC, BATCH>(p, v, beg, end, nbase, R, c, it, lane);
             add += 8ll * deg + 8;
         } else {
             if (W != R && lane == 0) st_color<ASYNC>(W + v, cv);
@@ -467,27 +593,38 @@ struct Shared {
     int pad;
 };
 
+// Block-wide First-Fit over the neighbours u <= vmax (see ff_thread), in
+// windows of kHubBmWords*32 colours; t_total = entries read.
 template <bool ASYNC>
-__device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R, Shared &sh)
+__device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, const int32_t *R, int32_t vmax,
+                        Shared &sh, int &t_total)
 {
     constexpr int kWin = kHubBmWords * 32;
+    if (threadIdx.x == 0) sh.tcount = 0;
     for (int base = 0;; base += kWin) {
         for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) sh.hub_bm[w] = 0u;
         if (threadIdx.x == 0) sh.first = INT_MAX;
         __syncthreads();
+        int t = 0;
         for (int i0 = 0; i0 < deg; i0 += kBlock * kBlockUnroll) {
             int c[kBlockUnroll];
+            bool take[kBlockUnroll];
 #pragma unroll
             for (int q = 0; q < kBlockUnroll; ++q) {
                 const int i = i0 + q * kBlock + threadIdx.x;
-                c[q] = (i < deg) ? ld_color<ASYNC>(R + nbase + __ldg(p.col_idx + beg + i)) : -1;
+                const int32_t u = (i < deg) ? nbase + __ldg(p.col_idx + beg + i) : 0;
+                take[q] = i < deg && u <= vmax;
+                c[q] = take[q] ? ld_color<ASYNC>(R + u) : -1;
+                t += take[q];
             }
 #pragma unroll
             for (int q = 0; q < kBlockUnroll; ++q) {
                 const int d = c[q] - base;
                 if (c[q] >= 0 && d >= 0 && d < kWin) atomicOr(&sh.hub_bm[d >> 5], 1u << (d & 31));
             }
+            if (!__syncthreads_or(threadIdx.x == kBlock - 1 ? (int)take[kBlockUnroll - 1] : 0)) break;
         }
+        if (base == 0 && t) atomicAdd(&sh.tcount, t);
         __syncthreads();
         for (int w = threadIdx.x; w < kHubBmWords; w += kBlock) {
             uint32_t f = ~sh.hub_bm[w];
@@ -496,9 +633,35 @@ __device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, c
         }
         __syncthreads();
         const int first = sh.first;
+        t_total = sh.tcount;
         __syncthreads();
         if (first != INT_MAX) return base + first;
         if (base > deg + 1) return deg + 1;  // not reached
+    }
+}
+
+// Block-wide push_clashes_thread: queue v's higher neighbours that hold k.
+template <bool ASYNC, bool BATCH>
+__device__ void push_clashes_block(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
+                                   const int32_t *R, int k, int it)
+{
+    const int deg = (int)(end - beg);
+    for (int i0 = 0; i0 < deg; i0 += kBlock * kBlockUnroll) {
+        int32_t u[kBlockUnroll];
+        bool side[kBlockUnroll];
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q) {
+            const int i = i0 + q * kBlock + threadIdx.x;
+            u[q] = (i < deg) ? nbase + __ldg(p.col_idx + end - 1 - i) : 0;
+            side[q] = i < deg && u[q] > v;
+        }
+        int c[kBlockUnroll];
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q) c[q] = side[q] ? ld_color<ASYNC>(R + u[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < kBlockUnroll; ++q)
+            if (side[q] && c[q] == k) push_one<BATCH>(p, u[q], it);
+        if (!__syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side[kBlockUnroll - 1] : 0)) break;
     }
 }
 
@@ -544,17 +707,20 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
     return any != 0;
 }
 
-template <bool ASYNC>
+template <bool ASYNC, bool BATCH>
 __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, int64_t beg, int64_t end, int32_t nbase,
-                             const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh)
+                             const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh, int it)
 {
     const int deg = (int)(end - beg);
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
+    int tf;
     if (op == OP_TENT) {
-        const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, sh);
+        const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, vmax, sh, tf);
         if (threadIdx.x == 0) st_color<ASYNC>(W + v, c);
-        add += 8ll * deg + 4;
+        add += 8ll * tf + 4;
     } else {
         const int cv = ld_color<ASYNC>(R + v);
         add += 4;
@@ -564,8 +730,9 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
             if (!ASYNC && threadIdx.x == 0) st_color<false>(p.cA + v, cv);
             add += 8ll * t + (d ? 4 : 0);
         } else if (d) {
-            const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, sh);
+            const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, vmax, sh, tf);
             if (threadIdx.x == 0) st_color<ASYNC>(W + v, c);
+            if (keep) push_clashes_block<ASYNC, BATCH>(p, v, beg, end, nbase, R, c, it);
             add += 8ll * deg + 8;
         } else {
             if (W != R && threadIdx.x == 0) st_color<ASYNC>(W + v, cv);
@@ -619,6 +786,11 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // other as uncoloured: that endpoint is the suspect when the tie-break
     // makes it the one to recolour.
     bool suspect = mid;
+    // GC_FF_KEEPERS: only lower neighbours count, and the sorted row is read
+    // up to v.
+    const bool keepers = (p.mode & GC_FF_KEEPERS) != 0;
+    const bool keep = keepers && deg > GC_KEEPERS_MIN_DEG;
+    int nread = 0;
     PT_BEGIN(t_g);
     if (thr) {
         for (int i = 0; i < deg; i += kUnroll) {
@@ -627,9 +799,15 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
                 u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
+                if (keep && u[q] > v) u[q] = -1;
+                nread += u[q] >= 0;
                 const uint32_t d = (uint32_t)(u[q] - cb32);  // in-chunk offset (wraps when outside)
                 const bool inside = u[q] >= 0 && d < 32u && !((hubmask >> d) & 1u);
                 if (inside && u[q] < v && !((midmask >> d) & 1u)) low |= 1u << d;
+                // A lower warp-path lane is coloured after this one and, with
+                // keepers, without looking at it: the pair is not checked
+                // unless this lane is.
+                if (keepers && inside && u[q] < v && ((midmask >> d) & 1u)) suspect = true;
                 outside[q] = u[q] >= 0 && !inside;
             }
             int c[kUnroll];
@@ -660,6 +838,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
                 if (b < 64u) ext |= 1ull << b;
                 if (outside[q] && c[q] == 0 && on_tie_side(tie, u[q], v)) suspect = true;
             }
+            if (keep && u[kUnroll - 1] < 0) break;  // row ended, or passed v
         }
     }
     __syncwarp();
@@ -701,7 +880,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     PT_END(p.st, 7, t_r);
     if (thr) {
         st_color<true>(C + v, mine);
-        mb += 8 + 8ll * deg + 4;
+        mb += 8 + 8ll * nread + 4;
     }
     __syncwarp();
     unsigned mm = midmask;
@@ -712,7 +891,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
         const int64_t ee = __shfl_sync(FULL_MASK, end, src);
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
-        vertex_warp<true>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane);
+        vertex_warp<true, false>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane, 0);
     }
     if (RING) {
         __syncwarp();
@@ -761,15 +940,6 @@ __device__ void publish_tile_done(const KParams &p, long long t, int lane)
 // one pass over a worklist
 // ------------------------------------------------------------------------
 
-template <bool BATCH>
-__device__ __forceinline__ void note_push_graph(const KParams &p, int32_t g, int it)
-{
-    if (BATCH) {
-        if (p.g_conflicts) atomicAdd(p.g_conflicts + g, 1ull);
-        if (p.g_rounds) atomicMax(p.g_rounds + g, it + 1);
-    }
-}
-
 struct PassIn {
     bool implicit;             // worklist is all of V (ids 0..n-1)
     const int32_t *wl;         // explicit tile worklist
@@ -787,6 +957,7 @@ __device__ __forceinline__ void push_lanes(const KParams &p, bool d, int32_t v, 
                                            int lane, bool stats)
 {
     DevState *st = p.st;
+    if (d && (p.mode & GC_FF_KEEPERS)) d = claim_push(p, v, it);  // not queued yet by a lower neighbour
     const unsigned m = __ballot_sync(FULL_MASK, d);
     if (!m) return;
     const int leader = __ffs(m) - 1;
@@ -819,7 +990,7 @@ __device__ __forceinline__ void chunk_ops(const KParams &p, Shared &sh, const E 
     if (implicit && deg > dmax) v = -1;  // coloured in another phase / stage
     const bool mid = v >= 0 && deg > p.t1;
     bool d = false;
-    if (v >= 0 && !mid) d = vertex_thread<ASYNC>(p, ent, op, v, beg, end, nbase, R, W, implicit, mb);
+    if (v >= 0 && !mid) d = vertex_thread<ASYNC, BATCH>(p, ent, op, v, beg, end, nbase, R, W, implicit, mb, it);
     unsigned mm = __ballot_sync(FULL_MASK, mid);
     while (mm) {
         const int src = __ffs(mm) - 1;
@@ -828,10 +999,17 @@ __device__ __forceinline__ void chunk_ops(const KParams &p, Shared &sh, const E 
         const int64_t bb = __shfl_sync(FULL_MASK, beg, src);
         const int64_t ee = __shfl_sync(FULL_MASK, end, src);
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
-        const bool dd = vertex_warp<ASYNC>(p, op, vv, bb, ee, nb, R, W, implicit, mb, sh.warp_bm[wid], lane);
+        const bool dd =
+            vertex_warp<ASYNC, BATCH>(p, op, vv, bb, ee, nb, R, W, implicit, mb, sh.warp_bm[wid], lane, it);
         if (lane == src) d = dd;
     }
-    if (push) push_lanes<BATCH>(p, d, v, deg, g, it, lane, true);
+    // A tentative pass over an explicit list (the degree tiers' round 0)
+    // keeps every vertex it coloured for the first repair pass, as the hub
+    // pass does: it did not track which ones read an uncoloured neighbour.
+    if (push) {
+        if (op == OP_TENT) push_lanes<BATCH>(p, v >= 0, v, deg, g, it, lane, false);
+        else push_lanes<BATCH>(p, d, v, deg, g, it, lane, true);
+    }
 }
 
 // A chunk of 32 consecutive ids in a pass over V: its uniform description
@@ -1151,6 +1329,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
         st->pass_hub[(q + 2) & (kRing - 1)] = 0;
     }
     int *out_hub = p.hub[it & 1];
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS);
 
     // hubs: one block per vertex, longest tasks first
     if (in.hn > 0) {
@@ -1165,9 +1344,9 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
-            const bool d = vertex_block<ASYNC>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh) ||
-                           op == OP_TENT;  // round 0: hubs are kept for the first repair pass
-            if (push && d && threadIdx.x == 0) {
+            bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
+                     op == OP_TENT;  // round 0: hubs are kept for the first repair pass
+            if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
                 atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
                 const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
                 if (idx < p.hub_cap) __stcg(out_hub + idx, v);
@@ -1265,6 +1444,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
     const bool snap = !twop && (!ASYNC || (p.mode & GC_REPAIR_SNAPSHOT) != 0);
     // Degree tiers (asynchronous RSOC): hubs, then mid-degree, then the rest.
     const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) != 0;
     unsigned nbl = gridDim.x;
     long long mb = 0;
     uint32_t phase = 0;  // parity bits of this warp's two staging barriers
@@ -1294,6 +1474,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
                 st_color<false>(p.cA + v, ASYNC ? 0 : 1);
                 if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
+                if (keep) p.mark[v] = 0;
                 if (!ASYNC) mb += 4;
             }
             const unsigned m = __ballot_sync(FULL_MASK, hub);

@@ -104,7 +104,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
                                 int32_t *colors_out, gc_stats *stats_out, void *stream)
 {
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
-    if (mode & ~(uint32_t)511) return GC_ERR_ARG;
+    if (!gc::mode_ok(mode)) return GC_ERR_ARG;
     if (n > kMaxN) return GC_ERR_TOO_LARGE;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
@@ -153,6 +153,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     p.nnz = nnz;
     p.cA = colors_out;
     p.cB = reinterpret_cast<int32_t *>(base + kOffB);
+    p.mark = (mode & GC_FF_KEEPERS) ? p.cB : nullptr;
     p.wl[0] = reinterpret_cast<int32_t *>(base + kOffWl0);
     p.wl[1] = reinterpret_cast<int32_t *>(base + kOffWl1);
     p.hub[0] = reinterpret_cast<int32_t *>(base + kOffHb0);

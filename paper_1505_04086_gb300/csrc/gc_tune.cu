@@ -1,0 +1,210 @@
+// Batch plans (one gc_color_batch call captured into a CUDA graph and
+// replayed) and the option autotuner for batches: the extern "C" entry
+// points gc_plan_* and gc_autotune_batch of include/gc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gc.h"
+#include "gc_ctx.h"
+#include "gc_internal.h"
+
+struct gc_plan {
+    gc_ctx *ctx = nullptr;               // private: its scratch never moves under the graph
+    cudaStream_t cap = nullptr;          // capture stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    gc::LastCall launched;               // host fields of the captured call
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess) return GC_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA;
+}
+
+bool batch_ok(const gc_batch *b)
+{
+    if (!b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0 ||
+        b->total_nnz >= (1ll << gc::kWorkBits))
+        return false;
+    if (b->G > 0 && (!b->vtx_off || !b->edge_off)) return false;
+    if (b->total_n > 0 && !b->row_ptr) return false;
+    if (b->total_nnz > 0 && !b->col_idx) return false;
+    return true;
+}
+
+int run_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o, int32_t *colors_out, cudaStream_t s)
+{
+    return gc::color_batch_impl(c, b->G, b->total_n, b->total_nnz, b->vtx_off, b->edge_off, nullptr, b->row_ptr,
+                                b->col_idx, mode, o, colors_out, nullptr, nullptr, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gc_plan_create(const gc_batch *b, int device, uint32_t mode, const gc_opts *opts, int32_t *colors_out,
+                   int32_t *rounds_out, int64_t *conflicts_out, gc_plan **out)
+{
+    if (!out) return GC_ERR_ARG;
+    *out = nullptr;
+    if (!batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out)) return GC_ERR_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    gc_plan *pl = new (std::nothrow) gc_plan();
+    if (!pl) return GC_ERR_OOM;
+    int rc = gc_ctx_create(&pl->ctx, device);
+    if (rc == GC_OK && cudaSetDevice(device) != cudaSuccess) rc = GC_ERR_CUDA;
+    if (rc == GC_OK) rc = gc::reserve_batch(pl->ctx, b->G, b->total_n, mode);
+    if (rc == GC_OK) rc = cuda_rc(cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking));
+    if (rc == GC_OK) rc = cuda_rc(cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+    if (rc == GC_OK) {
+        pl->ctx->capturing = true;
+        rc = gc::color_batch_impl(pl->ctx, b->G, b->total_n, b->total_nnz, b->vtx_off, b->edge_off, nullptr,
+                                  b->row_ptr, b->col_idx, mode, opts, colors_out, rounds_out, conflicts_out,
+                                  pl->cap);
+        pl->ctx->capturing = false;
+        // End the capture whatever happened, so that the stream is usable.
+        const cudaError_t e = cudaStreamEndCapture(pl->cap, &pl->graph);
+        if (rc == GC_OK) rc = cuda_rc(e);
+        else cudaGetLastError();
+    }
+    if (rc == GC_OK) rc = cuda_rc(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    if (rc == GC_OK) {
+        pl->launched = pl->ctx->last;
+        pl->ctx->last.pending = false;  // nothing ran yet
+        *out = pl;
+    } else {
+        gc_plan_destroy(pl);
+    }
+    cudaSetDevice(prev);
+    return rc;
+}
+
+int gc_plan_launch(gc_plan *pl, void *stream)
+{
+    if (!pl || !pl->exec) return GC_ERR_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(pl->ctx->device) != cudaSuccess) return GC_ERR_CUDA;
+    int rc = GC_OK;
+    if (pl->launched.empty) {
+        pl->ctx->last = pl->launched;  // empty batch: nothing was captured to run
+    } else {
+        rc = cuda_rc(cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
+        if (rc == GC_OK) pl->ctx->last = pl->launched;
+        else {
+            pl->ctx->last.pending = false;
+            pl->ctx->last.launch_status = rc;
+        }
+    }
+    cudaSetDevice(prev);
+    return rc;
+}
+
+int gc_plan_stats(gc_plan *pl, gc_stats *stats)
+{
+    if (!pl) return GC_ERR_ARG;
+    return gc_ctx_stats(pl->ctx, stats);
+}
+
+void gc_plan_destroy(gc_plan *pl)
+{
+    if (!pl) return;
+    if (pl->ctx) {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(pl->ctx->device);
+        if (pl->cap) cudaStreamSynchronize(pl->cap);
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        if (pl->graph) cudaGraphDestroy(pl->graph);
+        if (pl->cap) cudaStreamDestroy(pl->cap);
+        cudaGetLastError();
+        gc_ctx_destroy(pl->ctx);  // waits for the last replay
+        cudaSetDevice(prev);
+    }
+    delete pl;
+}
+
+int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t reps, int32_t *colors_out,
+                      gc_tune_result *out)
+{
+    if (!ctx || !out || !batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
+        reps > 64)
+        return GC_ERR_ARG;
+    memset(out, 0, sizeof *out);
+    // Device time of one option set: median over reps runs.
+    auto measure = [&](const gc_opts &o, float &ms) -> int {
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            int rc = run_batch(ctx, b, mode, &o, colors_out, nullptr);
+            gc_stats st;
+            memset(&st, 0, sizeof st);
+            if (rc == GC_OK) rc = gc_ctx_stats(ctx, &st);
+            if (rc != GC_OK) return rc;
+            t.push_back(st.elapsed_ms);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        ++out->evaluated;
+        return GC_OK;
+    };
+    const bool async = (mode & GC_SCHED_ASYNC) != 0;
+    // The knobs, each with its candidate values (0 = the library default).
+    struct Knob {
+        int32_t gc_opts::*field;
+        std::vector<int32_t> values;
+    };
+    std::vector<Knob> knobs = {
+        {&gc_opts::t1, {8, 16, 24, 32, 48, 62}},
+        {&gc_opts::t2, {128, 256, 512, 1024, 2048, 4096}},
+        {&gc_opts::tile, {32, 64, 128, 256, 512}},
+        {&gc_opts::blocks_per_sm, {1, 2, 0}},
+        {&gc_opts::tail, {-1, 256, 2048, 8192}},
+    };
+    if (async) knobs.push_back({&gc_opts::window, {0, -1}});
+    gc_opts best;  // the library defaults, spelled out
+    memset(&best, 0, sizeof best);
+    best.t1 = 32;
+    best.t2 = 2048;
+    best.tile = 64;
+    best.tail = 2048;
+    float best_ms = 0.f;
+    int rc = measure(best, best_ms);
+    if (rc != GC_OK) return rc;
+    out->default_ms = best_ms;
+    // Coordinate descent from the defaults: two sweeps over the knobs, each
+    // knob set to its fastest value with the others held.
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        bool moved = false;
+        for (const Knob &k : knobs) {
+            const int32_t cur = best.*(k.field);
+            for (int32_t v : k.values) {
+                if (v == cur) continue;
+                gc_opts o = best;
+                o.*(k.field) = v;
+                if (o.t1 > o.t2) continue;  // thread bin above the warp bin
+                float ms = 0.f;
+                if ((rc = measure(o, ms)) != GC_OK) return rc;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = o;
+                    moved = true;
+                }
+            }
+        }
+        if (!moved) break;
+    }
+    out->best = best;
+    out->best_ms = best_ms;
+    return GC_OK;
+}
+
+}  // extern "C"

@@ -46,6 +46,7 @@ GC_DEBUG_NO_TIEBREAK = 32
 GC_NO_COLOR_STATS = 64
 GC_REPAIR_SNAPSHOT = 128
 GC_TIERS = 256
+GC_FF_KEEPERS = 512
 
 # error word bits
 GC_EW_TIMEOUT = 1
@@ -80,6 +81,11 @@ class gc_batch(ctypes.Structure):
                 ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
 
 
+class gc_tune_result(ctypes.Structure):
+    _fields_ = [("best", gc_opts), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("evaluated", ctypes.c_int32)]
+
+
 class gc_server_info(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("waves", ctypes.c_uint64),
@@ -103,6 +109,13 @@ _SIGS = {
     "gc_ctx_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
     "gc_color_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32,
                                       ctypes.POINTER(gc_opts), _P, _P, _P, _P]),
+    "gc_plan_create": (ctypes.c_int, [ctypes.POINTER(gc_batch), ctypes.c_int, ctypes.c_uint32,
+                                      ctypes.POINTER(gc_opts), _P, _P, _P, ctypes.POINTER(_P)]),
+    "gc_plan_launch": (ctypes.c_int, [_P, _P]),
+    "gc_plan_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
+    "gc_plan_destroy": (None, [_P]),
+    "gc_autotune_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32, ctypes.c_int32, _P,
+                                         ctypes.POINTER(gc_tune_result)]),
     "gc_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts)]),
     "gc_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
@@ -277,6 +290,66 @@ def gc_color_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, edge
                                      ctypes.byref(o) if o is not None else None,
                                      _ptr(colors_out), _ptr(rounds_out), _ptr(conflicts_out),
                                      ctypes.c_void_p(_stream_handle(stream))))
+
+
+def _batch(G, total_n, total_nnz, vtx_off, edge_off, row_ptr, col_idx) -> gc_batch:
+    return gc_batch(int(G), int(total_n), int(total_nnz), _ptr(vtx_off), _ptr(edge_off),
+                    _ptr(row_ptr), _ptr(col_idx) if total_nnz else 0)
+
+
+def opts_dict(o: gc_opts) -> dict:
+    return {k: int(getattr(o, k)) for k, _ in gc_opts._fields_}
+
+
+def gc_autotune_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, edge_off, row_ptr, col_idx,
+                      mode: int, colors_out, reps: int = 3):
+    """Time option sets on the batch; returns (status, {"best": opts dict,
+    "best_ms", "default_ms", "evaluated"})."""
+    b = _batch(G, total_n, total_nnz, vtx_off, edge_off, row_ptr, col_idx)
+    r = gc_tune_result()
+    rc = load().gc_autotune_batch(ctypes.c_void_p(ctx), ctypes.byref(b), int(mode), int(reps),
+                                  _ptr(colors_out), ctypes.byref(r))
+    return int(rc), {"best": opts_dict(r.best), "best_ms": float(r.best_ms),
+                     "default_ms": float(r.default_ms), "evaluated": int(r.evaluated)}
+
+
+class Plan:
+    """A batch colouring captured in a CUDA graph (gc_plan_*): launch()
+    replays it on a stream, stats() waits and reports."""
+
+    def __init__(self, device: int, G: int, total_n: int, total_nnz: int, vtx_off, edge_off, row_ptr, col_idx,
+                 mode: int, colors_out, rounds_out=None, conflicts_out=None, opts=None):
+        b = _batch(G, total_n, total_nnz, vtx_off, edge_off, row_ptr, col_idx)
+        o = _opts(opts)
+        h = ctypes.c_void_p()
+        rc = load().gc_plan_create(ctypes.byref(b), int(device), int(mode),
+                                   ctypes.byref(o) if o is not None else None, _ptr(colors_out),
+                                   _ptr(rounds_out), _ptr(conflicts_out), ctypes.byref(h))
+        if rc != GC_OK:
+            raise GCError(rc, "gc_plan_create")
+        self.handle = int(h.value)
+        # the plan replays into these arrays: keep them alive with it
+        self._keep = (vtx_off, edge_off, row_ptr, col_idx, colors_out, rounds_out, conflicts_out)
+
+    def launch(self, stream=None) -> int:
+        return int(load().gc_plan_launch(ctypes.c_void_p(self.handle), ctypes.c_void_p(_stream_handle(stream))))
+
+    def stats(self, round_cap: int = 0):
+        st = gc_stats()
+        rs, rn = _stats_buffers(st, round_cap)
+        rc = load().gc_plan_stats(ctypes.c_void_p(self.handle), ctypes.byref(st))
+        return int(rc), stats_dict(st, rs, rn)
+
+    def close(self):
+        if self.handle:
+            load().gc_plan_destroy(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gc_color_noalloc(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, opts=None,

@@ -70,3 +70,22 @@ def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         gc.load()
+
+
+def test_mode_combinations_are_checked_on_the_host(lib):
+    # GC_FF_KEEPERS needs asynchronous RSOC with lower-keeps ties and in-place
+    # repairs; unknown bits are refused.  An empty batch keeps every other
+    # argument valid, and the check comes before any device work.
+    b = gc.gc_batch(0, 0, 0, 0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    K, A = gc.GC_FF_KEEPERS, gc.GC_SCHED_ASYNC
+    for mode in (K, K | A | gc.GC_ALG_TWO_PHASE, K | A | gc.GC_TIE_HIGHER_KEEPS,
+                 K | A | gc.GC_REPAIR_SNAPSHOT, K | A | gc.GC_DEBUG_NO_TIEBREAK, 1 << 10, 1 << 31):
+        assert lib.gc_plan_create(ctypes.byref(b), 0, mode, None, None, None, None,
+                                  ctypes.byref(h)) == gc.GC_ERR_ARG, mode
+        assert not h.value
+    r = gc.gc_tune_result()
+    assert lib.gc_autotune_batch(None, ctypes.byref(b), A | K, 3, None, ctypes.byref(r)) == gc.GC_ERR_ARG
+    assert lib.gc_plan_launch(None, None) == gc.GC_ERR_ARG
+    assert lib.gc_plan_stats(None, None) == gc.GC_ERR_ARG
+    lib.gc_plan_destroy(None)
