@@ -299,7 +299,8 @@ typedef struct {
  * Choose gc_opts for colouring this batch in `mode` by timing it: coordinate
  * descent from the defaults over t1 (largest degree coloured by one
  * thread), t2 (largest degree coloured by one warp; above it a block per
- * vertex), tile, blocks_per_sm, tail and, for GC_SCHED_ASYNC, window; each
+ * vertex), tile, blocks_per_sm and tail (window, which changes which graphs
+ * are coloured in id order and so the colour counts, stays automatic); each
  * candidate's cost is the median of `reps` (1..64) runs' device time
  * (CUDA events), and at most two sweeps are made.  Synchronous (legacy
  * default stream); colors_out (device, total_n entries) receives the

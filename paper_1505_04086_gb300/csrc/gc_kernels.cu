@@ -281,6 +281,14 @@ __device__ __forceinline__ int ff_thread(const E &ent, int64_t beg, int deg, int
     return __ffsll((long long)~mask);
 }
 
+// The neighbour bound of a tentative (round-0) First-Fit choice: with degree
+// tiers, higher neighbours may hold final colours of an earlier tier that no
+// later round inspects, so GC_FF_KEEPERS reads them there.
+__device__ __forceinline__ int32_t tent_vmax(const KParams &p, int32_t vmax)
+{
+    return (p.mode & GC_TIERS) ? INT32_MAX : vmax;
+}
+
 template <bool BATCH>
 __device__ __forceinline__ void note_push_graph(const KParams &p, int32_t g, int it)
 {
@@ -398,7 +406,7 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
     mb += (implicit ? 0 : 4) + 8;
     int t;
     if (op == OP_TENT) {
-        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R, vmax, t));
+        st_color<ASYNC>(W + v, ff_thread<ASYNC>(ent, beg, deg, nbase, R, tent_vmax(p, vmax), t));
         mb += 8ll * t + 4;
         return false;
     }
@@ -546,7 +554,7 @@ __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, in
     bool d = false;
     int tf;
     if (op == OP_TENT) {
-        const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, vmax, bm, lane, tf);
+        const int c = ff_warp<ASYNC>(p, beg, deg, nbase, R, tent_vmax(p, vmax), bm, lane, tf);
         if (lane == 0) st_color<ASYNC>(W + v, c);
         add += 8ll * tf + 4;
     } else {
@@ -718,7 +726,7 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
     bool d = false;
     int tf;
     if (op == OP_TENT) {
-        const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, vmax, sh, tf);
+        const int c = ff_block<ASYNC>(p, beg, deg, nbase, R, tent_vmax(p, vmax), sh, tf);
         if (threadIdx.x == 0) st_color<ASYNC>(W + v, c);
         add += 8ll * tf + 4;
     } else {
@@ -788,7 +796,9 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     bool suspect = mid;
     // GC_FF_KEEPERS: only lower neighbours count, and the sorted row is read
     // up to v.
-    const bool keepers = (p.mode & GC_FF_KEEPERS) != 0;
+    // With degree tiers the higher neighbours read here may be final
+    // colours of an earlier tier, which no later round inspects: read them.
+    const bool keepers = (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
     const bool keep = keepers && deg > GC_KEEPERS_MIN_DEG;
     int nread = 0;
     PT_BEGIN(t_g);
@@ -857,7 +867,34 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         // whatever its in-chunk neighbours pick.
         const bool narrow = __all_sync(FULL_MASK, (ext >> 31) == 0ull &&
                                                       __popc((uint32_t)ext) + __popc(low) <= 30);
-        if (narrow) {
+        // Chain: every lane depends on nothing in the chunk or on the lane
+        // just below it (consecutive ids along a mesh row).  Lane k's colour
+        // is then F_k(colour of lane k-1) with F_k(c) = (c == A) ? X : Y
+        // (A, Y its first free colour, X its second), a form closed under
+        // composition, so an inclusive scan of the F's over the lanes gives
+        // every colour in five shuffle steps.
+        const bool chain = __all_sync(FULL_MASK, low == 0u || low == (1u << ((lane + 31) & 31)));
+        if (chain) {
+            const int a = __ffsll((long long)~ext);
+            int A = 0, X = a, Y = a;  // low == 0: constant a
+            if (low) {
+                A = a;
+                X = __ffsll((long long)~(ext | (1ull << (a - 1))));
+            }
+            for (int d = 1; d < 32; d <<= 1) {
+                const int A2 = __shfl_up_sync(FULL_MASK, A, d);
+                const int X2 = __shfl_up_sync(FULL_MASK, X, d);
+                const int Y2 = __shfl_up_sync(FULL_MASK, Y, d);
+                if (lane >= d) {  // compose: this lane's function after lane-d's
+                    const int nX = (X2 == A) ? X : Y;
+                    const int nY = (Y2 == A) ? X : Y;
+                    A = A2;
+                    X = nX;
+                    Y = nY;
+                }
+            }
+            mine = X;  // lane 0's function is constant, so the composition is too
+        } else if (narrow) {
             uint32_t e32 = (uint32_t)ext;
             for (int k = k0; k <= k1; ++k) {
                 const int cand = __ffs(~e32);

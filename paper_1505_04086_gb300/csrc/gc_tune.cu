@@ -156,8 +156,9 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t rep
         ++out->evaluated;
         return GC_OK;
     };
-    const bool async = (mode & GC_SCHED_ASYNC) != 0;
-    // The knobs, each with its candidate values (0 = the library default).
+    // The knobs (only those that leave the method's result alone: window,
+    // which decides which graphs are coloured in id order, changes colour
+    // counts and is not tuned), each with its candidate values.
     struct Knob {
         int32_t gc_opts::*field;
         std::vector<int32_t> values;
@@ -169,7 +170,6 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t rep
         {&gc_opts::blocks_per_sm, {1, 2, 0}},
         {&gc_opts::tail, {-1, 256, 2048, 8192}},
     };
-    if (async) knobs.push_back({&gc_opts::window, {0, -1}});
     gc_opts best;  // the library defaults, spelled out
     memset(&best, 0, sizeof best);
     best.t1 = 32;

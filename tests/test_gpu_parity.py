@@ -233,3 +233,22 @@ def test_checked_mode_passes_on_real_results(ctx):
         for mode in (RSOC | DET, RSOC | ASYNC, TWOP | ASYNC):
             rc, _, st = run(ctx, g, mode | gc.GC_CHECKED | gc.GC_VALIDATE)
             assert rc == gc.GC_OK and st["error_word"] == 0
+
+
+@pytest.mark.parametrize("make", [lambda: I.tri2d(64, 64), lambda: I.tri2d(50, 70, jitter=0.3, seed=9),
+                                  lambda: I.tri2d(300, 7), lambda: I.kuhn3d(12),
+                                  lambda: I.kuhn3d(9, permute=False), lambda: I.rgg(12000, 12.0, seed=2)],
+                         ids=["tri64", "tri_jit", "tri_narrow", "kuhn12", "kuhn9_nat", "rgg12k"])
+def test_ordered_round0_is_sequential_first_fit(ctx, make):
+    # A graph of at most 16384 vertices whose degrees all fit one thread is
+    # coloured in round 0 by one warp in id order, every lane seeing the final
+    # colours of all lower neighbours (in-chunk ones through the lane scan or
+    # the shuffle walk) and none of the higher ones: exactly Algorithm 1.
+    g = make()
+    assert g.n <= 16384 and int(np.diff(g.row_ptr).max()) <= 62
+    ff = O.ff(g)
+    for _ in range(3):
+        rc, col, st = run(ctx, g, gc.GC_SCHED_ASYNC, {"t1": 62, "t2": 4096})
+        assert rc == gc.GC_OK
+        assert np.array_equal(col, ff), f"first diff at {np.nonzero(col != ff)[0][:5]}"
+        assert st["conflicts"] == 0 and st["rounds"] == 1
