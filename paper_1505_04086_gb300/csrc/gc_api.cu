@@ -126,6 +126,8 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.gstat = c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();
     p.olist = c->olist.as<int32_t>();
+    p.pitems = c->pitems.as<int64_t>();
+    p.pitems_cap = c->pitems_cap;
     p.cB = c->cB.as<int32_t>();
     p.mark = (mode & GC_FF_KEEPERS) ? p.cB : nullptr;
     p.wl[0] = c->wl0.as<int32_t>();
@@ -327,6 +329,12 @@ int gc_ctx_create(gc_ctx **out, int device)
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             if (rc == GC_OK && c->occ[a][b] < 1) rc = GC_ERR_CUDA;
+    if (rc == GC_OK) {
+        // one warp-group item per warp of the largest grid
+        const int occ = std::max(std::max(c->occ[0][0], c->occ[0][1]), std::max(c->occ[1][0], c->occ[1][1]));
+        c->pitems_cap = c->num_sms * occ * gc::kWarps;
+        if (!c->pitems.reserve((size_t)c->pitems_cap * sizeof(int64_t))) rc = GC_ERR_OOM;
+    }
     cudaSetDevice(prev);
     if (rc != GC_OK) {
         gc_ctx_destroy(c);
@@ -344,7 +352,8 @@ void gc_ctx_destroy(gc_ctx *c)
     cudaSetDevice(c->device);
     if (c->ev_done) cudaEventSynchronize(c->ev_done);
     for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
-                   &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->stage_rp, &c->stage_ci,
+                   &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->pitems, &c->stage_rp,
+                   &c->stage_ci,
                    &c->stage_col})
         b->release();
     if (c->st_host) cudaFreeHost(c->st_host);

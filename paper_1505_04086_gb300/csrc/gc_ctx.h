@@ -69,6 +69,8 @@ struct gc_ctx {
     int occ[2][2] = {{0, 0}, {0, 0}};
     // scratch
     gc::Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done, gstat, uofs, olist;
+    gc::Buf pitems;                         // round-0 warp groups: one item per warp of the grid
+    int32_t pitems_cap = 0;
     gc::Buf stage_rp, stage_ci, stage_col;  // gc_color host staging
     gc::DevState *st_host = nullptr;        // pinned
     int32_t *rs_host = nullptr;             // pinned round sizes

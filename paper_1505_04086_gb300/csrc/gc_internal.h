@@ -29,6 +29,8 @@ constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entrie
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
+constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order
+constexpr int kPipeMinChunks = 8;       // fewest chunks per warp of a group
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 
@@ -59,7 +61,9 @@ struct GraphStat {
     unsigned long long near_lower;  // locality sample: lower neighbours within kNearIds
     unsigned long long all_lower;   // locality sample: all lower neighbours
     unsigned int hubs;              // vertices of degree > t2
-    unsigned int ordered;           // coloured in id order by one warp in round 0
+    unsigned int ordered;           // coloured in id order in round 0
+    unsigned int mids;              // nonzero: some vertex has t1 < degree <= t2
+    unsigned int group;             // warps colouring it in id order together (0: one)
 };
 
 // Device-resident state of one colouring launch.  Zeroed before each launch.
@@ -82,7 +86,8 @@ struct DevState {
     int distinct;
     unsigned long long dbg[16];      // phase cycle counters (builds with GC_PHASE_TIMING only)
     int seq_claim;                   // round 0: next ordered graph to claim
-    int n_ordered;                   // number of ordered graphs
+    int n_ordered;                   // number of ordered graphs coloured by one warp
+    int n_pitems;                    // warps of the groups colouring one graph in id order
     long long n_uchunks;             // chunks of the graphs that are not ordered
     int window;                      // number of graphs coloured in id order in round 0
     unsigned long long t_start;      // globaltimer at kernel start (ns)
@@ -127,6 +132,8 @@ struct KParams {
     int64_t *uofs;             // G+1: prefix sums of the unordered graphs' chunk counts
     int32_t *olist;            // G: the ordered graphs
     int32_t *mark;             // GC_FF_KEEPERS: n entries, last iteration a vertex was queued in + 1
+    int64_t *pitems;           // round 0: (graph, warp, group size) of each grouped warp
+    int32_t pitems_cap;        // its capacity (>= the grid's warps)
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

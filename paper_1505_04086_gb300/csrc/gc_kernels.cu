@@ -766,6 +766,76 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
 // first repair worklist instead of all of V.
 constexpr uint16_t kRingGlobal = 0xFFFFu;  // ring entry: read this id's colour from memory
 
+// The colours the 32 lanes of a chunk take when they are coloured in lane
+// (id) order: ext = colours of a lane's neighbours outside the chunk (bit
+// c-1 for colour c), low = the lower lanes it is adjacent to, act = the lane
+// has a vertex to colour.  Lanes in no lane's `low` and with act false do not
+// take part; their result is 0.
+__device__ __forceinline__ int resolve_in_order(unsigned long long ext, unsigned low, bool act, int lane)
+{
+    int mine = act ? __ffsll((long long)~ext) : 0;
+    // In-chunk dependencies: walk only the lanes between the first lane some
+    // lane depends on and the last dependent lane, in id order.  Branch-free:
+    // every lane recomputes its candidate each step and lane k's is taken.
+    const unsigned dependent = __ballot_sync(FULL_MASK, low != 0u);
+    if (dependent) {
+        const unsigned needed = __reduce_or_sync(FULL_MASK, low);
+        const int k0 = __ffs(needed) - 1;
+        const int k1 = 31 - __clz(dependent);
+        // 32-bit masks suffice when every lane keeps a free colour in 1..31
+        // whatever its in-chunk neighbours pick.
+        const bool narrow = __all_sync(FULL_MASK, (ext >> 31) == 0ull &&
+                                                      __popc((uint32_t)ext) + __popc(low) <= 30);
+        // Chain: every lane depends on nothing in the chunk or on the lane
+        // just below it (consecutive ids along a mesh row).  Lane k's colour
+        // is then F_k(colour of lane k-1) with F_k(c) = (c == A) ? X : Y
+        // (A, Y its first free colour, X its second), a form closed under
+        // composition, so an inclusive scan of the F's over the lanes gives
+        // every colour in five shuffle steps.
+        const bool chain = __all_sync(FULL_MASK, low == 0u || low == (1u << ((lane + 31) & 31)));
+        if (chain) {
+            const int a = __ffsll((long long)~ext);
+            int A = 0, X = a, Y = a;  // low == 0: constant a
+            if (low) {
+                A = a;
+                X = __ffsll((long long)~(ext | (1ull << (a - 1))));
+            }
+            for (int d = 1; d < 32; d <<= 1) {
+                const int A2 = __shfl_up_sync(FULL_MASK, A, d);
+                const int X2 = __shfl_up_sync(FULL_MASK, X, d);
+                const int Y2 = __shfl_up_sync(FULL_MASK, Y, d);
+                if (lane >= d) {  // compose: this lane's function after lane-d's
+                    const int nX = (X2 == A) ? X : Y;
+                    const int nY = (Y2 == A) ? X : Y;
+                    A = A2;
+                    X = nX;
+                    Y = nY;
+                }
+            }
+            mine = X;  // lane 0's function is constant, so the composition is too
+        } else if (narrow) {
+            uint32_t e32 = (uint32_t)ext;
+            for (int k = k0; k <= k1; ++k) {
+                const int cand = __ffs(~e32);
+                const int ck = __shfl_sync(FULL_MASK, cand, k);
+                mine = (lane == k) ? cand : mine;
+                e32 |= ((low >> k) & 1u) << (ck - 1);
+            }
+            if (lane > k1) mine = __ffs(~e32);
+        } else {
+            for (int k = k0; k <= k1; ++k) {
+                const int cand = __ffsll((long long)~ext);
+                const int ck = __shfl_sync(FULL_MASK, cand, k);
+                mine = (lane == k) ? cand : mine;
+                ext |= (unsigned long long)((low >> k) & 1u) << (ck - 1);
+            }
+            if (lane > k1) mine = __ffsll((long long)~ext);
+        }
+        if (!act) mine = 0;
+    }
+    return mine;
+}
+
 // RING: the chunk belongs to an ordered graph that this warp colours in id
 // order from v0; ids in [max(v0, cbase - kRingIds), cbase) were coloured by
 // this warp and their colours sit in `ring`; with skip_higher no id above
@@ -854,66 +924,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     __syncwarp();
     PT_END(p.st, 6, t_g);
     PT_BEGIN(t_r);
-    int mine = thr ? __ffsll((long long)~ext) : 0;
-    // In-chunk dependencies: walk only the lanes between the first lane some
-    // lane depends on and the last dependent lane, in id order.  Branch-free:
-    // every lane recomputes its candidate each step and lane k's is taken.
-    const unsigned dependent = __ballot_sync(FULL_MASK, low != 0u);
-    if (dependent) {
-        const unsigned needed = __reduce_or_sync(FULL_MASK, low);
-        const int k0 = __ffs(needed) - 1;
-        const int k1 = 31 - __clz(dependent);
-        // 32-bit masks suffice when every lane keeps a free colour in 1..31
-        // whatever its in-chunk neighbours pick.
-        const bool narrow = __all_sync(FULL_MASK, (ext >> 31) == 0ull &&
-                                                      __popc((uint32_t)ext) + __popc(low) <= 30);
-        // Chain: every lane depends on nothing in the chunk or on the lane
-        // just below it (consecutive ids along a mesh row).  Lane k's colour
-        // is then F_k(colour of lane k-1) with F_k(c) = (c == A) ? X : Y
-        // (A, Y its first free colour, X its second), a form closed under
-        // composition, so an inclusive scan of the F's over the lanes gives
-        // every colour in five shuffle steps.
-        const bool chain = __all_sync(FULL_MASK, low == 0u || low == (1u << ((lane + 31) & 31)));
-        if (chain) {
-            const int a = __ffsll((long long)~ext);
-            int A = 0, X = a, Y = a;  // low == 0: constant a
-            if (low) {
-                A = a;
-                X = __ffsll((long long)~(ext | (1ull << (a - 1))));
-            }
-            for (int d = 1; d < 32; d <<= 1) {
-                const int A2 = __shfl_up_sync(FULL_MASK, A, d);
-                const int X2 = __shfl_up_sync(FULL_MASK, X, d);
-                const int Y2 = __shfl_up_sync(FULL_MASK, Y, d);
-                if (lane >= d) {  // compose: this lane's function after lane-d's
-                    const int nX = (X2 == A) ? X : Y;
-                    const int nY = (Y2 == A) ? X : Y;
-                    A = A2;
-                    X = nX;
-                    Y = nY;
-                }
-            }
-            mine = X;  // lane 0's function is constant, so the composition is too
-        } else if (narrow) {
-            uint32_t e32 = (uint32_t)ext;
-            for (int k = k0; k <= k1; ++k) {
-                const int cand = __ffs(~e32);
-                const int ck = __shfl_sync(FULL_MASK, cand, k);
-                mine = (lane == k) ? cand : mine;
-                e32 |= ((low >> k) & 1u) << (ck - 1);
-            }
-            if (lane > k1) mine = __ffs(~e32);
-        } else {
-            for (int k = k0; k <= k1; ++k) {
-                const int cand = __ffsll((long long)~ext);
-                const int ck = __shfl_sync(FULL_MASK, cand, k);
-                mine = (lane == k) ? cand : mine;
-                ext |= (unsigned long long)((low >> k) & 1u) << (ck - 1);
-            }
-            if (lane > k1) mine = __ffsll((long long)~ext);
-        }
-        if (!thr) mine = 0;
-    }
+    const int mine = resolve_in_order(ext, low, thr, lane);
     PT_END(p.st, 7, t_r);
     if (thr) {
         st_color<true>(C + v, mine);
@@ -1218,6 +1229,178 @@ __device__ __noinline__ void seq_graph(const KParams &p, Shared &sh, int32_t g, 
 // Chunk vc of a pass: direct (ids 32*vc.., up to n) or, in the round-0
 // tentative pass, numbered over the graphs that are not ordered (uofs holds
 // their prefix sums of chunk counts).
+// ------------------------------------------------------------------------
+// ordered round 0 by a group of warps (pipelined id order)
+// ------------------------------------------------------------------------
+
+constexpr unsigned long long kPipeTimeoutNs = 2000000000ull;  // 2 s per chunk
+
+// One chunk of a graph that a group of warps colours in id order: a lane
+// is coloured once every lower neighbour is (those outside the chunk are
+// polled in memory, where other warps of the group write them; those inside
+// are resolved here), from those colours only.  Nothing above a vertex is
+// read, so the result is exactly sequential First-Fit (Algorithm 1), while
+// the chunks of the group's warps overlap wherever they do not depend on
+// each other (along a mesh, a wavefront over its rows).  Lanes whose lower
+// neighbours are all coloured go first, in id order; the others wait.
+// Returns false if a wait timed out (error word set).
+template <class E>
+__device__ bool chunk_pipe(const KParams &p, const E &ent, int32_t cb, int32_t v, int64_t beg, int deg,
+                           int32_t nbase, int32_t *C, long long &mb, int lane)
+{
+    const bool act = v >= 0;
+    unsigned done = __ballot_sync(FULL_MASK, !act);
+    int mine = 0;
+    unsigned long long t0 = 0;
+    unsigned backoff = 32;
+    while (done != FULL_MASK) {
+        const bool todo = !((done >> lane) & 1u);
+        unsigned long long ext = 0;
+        unsigned low = 0;
+        bool pend = false;
+        int nlo = 0;
+        if (todo) {
+            for (int i = 0; i < deg; i += kUnroll) {
+                int u[kUnroll];
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
+                    if (u[q] > v) u[q] = -1;  // higher neighbours are not looked at
+                }
+                int c[kUnroll];
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    const uint32_t d = (uint32_t)(u[q] - cb);
+                    const bool inside = u[q] >= 0 && d < 32u;
+                    if (inside) low |= 1u << d;
+                    c[q] = (u[q] >= 0 && !inside) ? ld_color<true>(C + u[q]) : 0;
+                    if (u[q] >= 0 && !inside && c[q] == 0) pend = true;
+                    nlo += u[q] >= 0;
+                }
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    const unsigned b = (unsigned)(c[q] - 1);
+                    if (b < 64u) ext |= 1ull << b;
+                }
+                if (u[kUnroll - 1] < 0) break;  // row ended, or passed v (rows are sorted)
+            }
+        }
+        // colours of lower lanes finished earlier in this call
+        const unsigned need = __reduce_or_sync(FULL_MASK, todo ? (low & done) : 0u);
+        for (unsigned m = need; m; m &= m - 1) {
+            const int j = __ffs(m) - 1;
+            const int cj = __shfl_sync(FULL_MASK, mine, j);
+            if (todo && ((low >> j) & 1u)) ext |= 1ull << (cj - 1);
+        }
+        low &= ~done;
+        // the lanes that can go now: no uncoloured neighbour outside, and every
+        // lower lane they depend on goes too
+        unsigned S = __ballot_sync(FULL_MASK, todo && !pend);
+        for (;;) {
+            const unsigned S2 = __ballot_sync(FULL_MASK, ((S >> lane) & 1u) && (low & ~S) == 0u);
+            if (S2 == S) break;
+            S = S2;
+        }
+        if (S) {
+            const bool in = (S >> lane) & 1u;
+            const int m = resolve_in_order(ext, in ? low : 0u, in, lane);
+            if (in) {
+                mine = m;
+                st_color<true>(C + v, mine);
+                mb += 8 + 8ll * nlo + 4;
+            }
+            done |= S;
+            continue;
+        }
+        // nothing can go: the group's other warps still colour lower ids
+        if (t0 == 0) {
+            t0 = global_timer();
+        } else if (global_timer() - t0 > kPipeTimeoutNs) {
+            if (lane == 0) atomicOr(&p.st->error, GC_EW_TIMEOUT);
+            return false;
+        }
+        __nanosleep(backoff);
+        backoff = min(backoff * 2u, 1024u);
+    }
+    return true;
+}
+
+// Warp j of a group of K colours chunks j, j+K, j+2K, ... of graph g (ids
+// v0..v1-1) with chunk_pipe, staging each chunk's adjacency segment one
+// chunk ahead.  Only graphs without hubs or warp-path vertices are grouped.
+template <bool BATCH>
+__device__ __noinline__ void pipe_graph(const KParams &p, Shared &sh, int32_t g, long long v0, long long v1, int j,
+                                        int K, int32_t *C, long long &mb, uint32_t &phase, int lane, int wid)
+{
+    const long long lim16 = (p.nnz * 4) & ~15ll;
+    const int32_t *rp = p.row_ptr;
+    int64_t eo = 0;
+    int32_t nbase = 0;
+    if (BATCH) {
+        rp = p.row_ptr + (p.rp_off ? __ldg(p.rp_off + g) : v0 + g);
+        eo = __ldg(p.edge_off + g);
+        nbase = (int32_t)v0;
+    }
+    const long long ng = v1 - v0;
+    const long long nck = (ng + 31) / 32;
+    auto load_rows = [&](long long k, int32_t &b, int32_t &e) {
+        const long long lv = k * 32 + lane;
+        b = e = 0;
+        if (k < nck && lv < ng) {
+            b = __ldg(rp + lv);
+            e = __ldg(rp + lv + 1);
+        }
+    };
+    auto issue = [&](long long k, int slot, int32_t b, int32_t e) -> long long {
+        long long soff = -1;
+        if (k < nck) {
+            const int last = (int)min(31ll, ng - 1 - k * 32);
+            const long long s0 = eo + __shfl_sync(FULL_MASK, b, 0);
+            const long long e0 = eo + __shfl_sync(FULL_MASK, e, last);
+            const long long a0 = (s0 * 4) & ~15ll, a1 = (e0 * 4 + 15) & ~15ll;
+            if (e0 > s0 && a1 - a0 <= (long long)kSegCap * 4 && a1 <= lim16) {
+                soff = a0 >> 2;
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&sh.mbar[wid][slot], (uint32_t)(a1 - a0));
+                    bulk_copy_g2s(sh.seg[wid][slot], reinterpret_cast<const char *>(p.col_idx) + a0,
+                                  (uint32_t)(a1 - a0), &sh.mbar[wid][slot]);
+                }
+            }
+        }
+        return soff;
+    };
+    int32_t b0, e0, b1, e1;
+    load_rows(j, b0, e0);
+    int slot = 0;
+    long long soff0 = issue(j, 0, b0, e0);
+    for (long long k = j; k < nck; k += K) {
+        load_rows(k + K, b1, e1);
+        const long long soff1 = issue(k + K, slot ^ 1, b1, e1);
+        bool staged = soff0 >= 0;
+        bool ok = true;
+        if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = ok = false;
+        const int32_t cb = (int32_t)(v0 + k * 32);
+        const int32_t v = k * 32 + lane < ng ? cb + lane : -1;
+        if (ok) {
+            if (staged)
+                ok = chunk_pipe(p, StagedEnts{sh.seg[wid][slot], soff0}, cb, v, eo + b0, e0 - b0, nbase, C, mb,
+                                lane);
+            else
+                ok = chunk_pipe(p, GlobalEnts{p.col_idx}, cb, v, eo + b0, e0 - b0, nbase, C, mb, lane);
+        }
+        __syncwarp();
+        if (!ok) {  // let the copy in flight land before leaving
+            if (soff1 >= 0) wait_stage(p, sh, slot ^ 1, phase, wid);
+            return;
+        }
+        b0 = b1;
+        e0 = e1;
+        soff0 = soff1;
+        slot ^= 1;
+    }
+}
+
 template <bool BATCH>
 __device__ __forceinline__ void chunk_of(const KParams &p, long long vc, bool virt, long long n, long long &cb,
                                          long long &cend)
@@ -1261,7 +1444,18 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
     const long long lim16 = (p.nnz * 4) & ~15ll;
 
     if (ordered) {
-        // Phase A: ordered graphs, one warp each, largest work first claimed.
+        // Phase A: ordered graphs.  Warp w < n_pitems belongs to a group
+        // colouring one graph together (all of a group's warps are resident
+        // and start at once); then one warp per remaining ordered graph.
+        const int gw = blockIdx.x * kWarps + wid;
+        if (gw < ld_volatile(&st->n_pitems)) {
+            const long long item = __ldcg(p.pitems + gw);
+            const int32_t g = (int32_t)(item >> 20);
+            const int j = (int)((item >> 10) & 1023), K = (int)(item & 1023) + 1;
+            const long long v0 = BATCH ? __ldg(p.vtx_off + g) : 0;
+            const long long v1 = BATCH ? __ldg(p.vtx_off + g + 1) : p.n;
+            pipe_graph<BATCH>(p, sh, g, v0, v1, j, K, W, mb, phase, lane, wid);
+        }
         const int nord = ld_volatile(&st->n_ordered);
         const bool tiered = (p.mode & GC_TIERS) != 0;
         for (;;) {
@@ -1418,33 +1612,106 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
     }
 }
 
-// Block 0: decide which graphs are coloured in id order by one warp (round
-// 0 of the asynchronous mode), list them, and number the chunks of the other
-// graphs (prefix sums in uofs).  window 1: every graph; 0: graphs of at most
+// Sum of x over the block (every thread gets it).  Uses sh.hub_bm as
+// scratch; all threads must call it.
+__device__ long long block_sum(long long x, Shared &sh)
+{
+    long long *red = reinterpret_cast<long long *>(sh.hub_bm);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL_MASK, x, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = x;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Block 0: decide which graphs are coloured in id order in round 0 of the
+// asynchronous mode (window 1: every graph; 0: graphs of at most
 // kOrderedSmall vertices and graphs whose sampled lower neighbours mostly lie
-// within kNearIds ids; else none.
+// within kNearIds ids; else none), and how: a graph without hubs or
+// warp-path vertices whose chunks exceed the per-warp share of all ordered
+// chunks gets a group of warps (pipe_graph; the groups together take at
+// most three quarters of the grid's warps), any other ordered graph one
+// warp.  Also numbers the chunks of the graphs that are not ordered
+// (prefix sums in uofs).
 template <bool BATCH>
 __device__ void plan_ordering(const KParams &p, Shared &sh)
 {
     DevState *st = p.st;
     const int window = p.window;
+    const bool tiers = (p.mode & GC_TIERS) != 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long warps = (long long)gridDim.x * kWarps;
+    const long long budget = min(warps, (long long)p.pitems_cap) * 3 / 4;
+    auto graph_n = [&](int g) -> long long {
+        return BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
+    };
+    auto is_ordered = [&](int g, long long ng) -> bool {
+        const GraphStat &gs = p.gstat[g];
+        // Small graphs are ordered too: coloured all at once they would be
+        // coloured almost simultaneously, whatever their numbering.
+        return ng > 0 && (window == 1 || (window == 0 && (ng <= kOrderedSmall ||
+                                                          (gs.all_lower > 0 && 2 * gs.near_lower >= gs.all_lower))));
+    };
+    auto groupable = [&](int g) -> bool {
+        return !tiers && p.gstat[g].hubs == 0 && p.gstat[g].mids == 0;
+    };
+    // Ordered chunks in all, and the per-warp share of them.
+    long long T = 0;
+    for (int g0 = 0; g0 < p.G; g0 += kBlock) {
+        const int g = g0 + threadIdx.x;
+        long long c = 0;
+        if (g < p.G) {
+            const long long ng = graph_n(g);
+            if (is_ordered(g, ng)) c = (ng + 31) / 32;
+        }
+        T += block_sum(c, sh);
+    }
+    long long target = max((T + warps - 1) / max(warps, 1ll), (long long)kPipeMinChunks);
+    auto group_of = [&](long long chunks) -> int {
+        return chunks > target ? (int)min((chunks + target - 1) / target, (long long)kPipeMaxK) : 1;
+    };
+    for (;;) {  // widen the share until the groups fit the budget
+        long long need = 0;
+        for (int g0 = 0; g0 < p.G; g0 += kBlock) {
+            const int g = g0 + threadIdx.x;
+            long long k = 0;
+            if (g < p.G) {
+                const long long ng = graph_n(g);
+                if (is_ordered(g, ng) && groupable(g)) {
+                    const int K = group_of((ng + 31) / 32);
+                    if (K > 1) k = K;
+                }
+            }
+            need += block_sum(k, sh);
+        }
+        if (need <= budget || target > (1ll << 40)) break;
+        target *= 2;
+    }
     long long carry = 0;
     long long *warp_tot = reinterpret_cast<long long *>(sh.hub_bm);  // block-local scratch
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int g0 = 0; g0 < p.G; g0 += kBlock) {
         const int g = g0 + threadIdx.x;
         long long chunks = 0;
         if (g < p.G) {
-            const long long ng = BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
-            const GraphStat gs = p.gstat[g];
-            // Small graphs are ordered too: coloured all at once they would
-            // be coloured almost simultaneously, whatever their numbering.
-            const bool ord = ng > 0 && (window == 1 || (window == 0 && (ng <= kOrderedSmall ||
-                                                                        (gs.all_lower > 0 &&
-                                                                         2 * gs.near_lower >= gs.all_lower))));
+            const long long ng = graph_n(g);
+            const bool ord = is_ordered(g, ng);
+            int K = 1;
+            if (ord && groupable(g)) K = group_of((ng + 31) / 32);
             p.gstat[g].ordered = ord;
-            if (ord) p.olist[atomicAdd(&st->n_ordered, 1)] = g;
-            else chunks = (ng + 31) / 32;
+            p.gstat[g].group = K > 1 ? K : 0;
+            if (ord && K > 1) {
+                const int base = atomicAdd(&st->n_pitems, K);
+                for (int j = 0; j < K; ++j)
+                    p.pitems[base + j] = ((long long)g << 20) | ((long long)j << 10) | (long long)(K - 1);
+            } else if (ord) {
+                p.olist[atomicAdd(&st->n_ordered, 1)] = g;
+            } else {
+                chunks = (ng + 31) / 32;
+            }
         }
         // block-wide exclusive scan of chunks
         long long x = chunks;
@@ -1509,6 +1776,8 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 hub = (end - beg) > p.t2;
                 midv = tiers && !hub && (end - beg) > p.t1;
                 if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
+                if (ASYNC && !hub && (end - beg) > p.t1 && __ldcg(&p.gstat[g].mids) == 0u)
+                    atomicOr(&p.gstat[g].mids, 1u);
                 st_color<false>(p.cA + v, ASYNC ? 0 : 1);
                 if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
                 if (keep) p.mark[v] = 0;

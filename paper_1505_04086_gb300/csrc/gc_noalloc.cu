@@ -48,7 +48,9 @@ constexpr size_t kOffHb0 = kOffWl1 + kVec;
 constexpr size_t kOffHb1 = kOffHb0 + kVec;
 constexpr size_t kOffHubAll = kOffHb1 + kVec;
 constexpr size_t kOffMidAll = kOffHubAll + kVec;
-constexpr size_t kNoAllocBytes = kOffMidAll + kVec;
+constexpr int32_t kPitems = 8192;  // round-0 warp groups: items for grids of up to 8192 warps
+constexpr size_t kOffPitems = kOffMidAll + kVec;
+constexpr size_t kNoAllocBytes = kOffPitems + align256(kPitems * sizeof(int64_t));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -165,6 +167,8 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     p.gstat = reinterpret_cast<gc::GraphStat *>(base + kOffGstat);
     p.uofs = reinterpret_cast<int64_t *>(base + kOffUofs);
     p.olist = reinterpret_cast<int32_t *>(base + kOffOlist);
+    p.pitems = reinterpret_cast<int64_t *>(base + kOffPitems);
+    p.pitems_cap = kPitems;
     p.st = reinterpret_cast<gc::DevState *>(base + kOffState);
     p.round_sizes = reinterpret_cast<int32_t *>(base + kOffRounds);
     p.round_sizes_cap = kRoundSizes;

@@ -121,3 +121,18 @@ def test_async_batch_quality_per_graph(ctx):
             assert bad == 0
             ff = int(O.ff(sub).max())
             assert mx <= 1.1 * ff, f"graph {g} kind {b.kind[g]}: {mx} vs first-fit {ff}"
+
+
+def test_ordered_batch_is_sequential_first_fit_per_graph(ctx):
+    # With window 1 every graph of the batch is coloured in id order in round
+    # 0 (big ones by warp groups, the rest one warp each): each graph's
+    # colouring is exactly sequential First-Fit of that graph alone.
+    b = I.batch(40, 1 << 8, 1 << 16, seed=41, threads=8)
+    assert int(np.diff(b.row_ptr).max()) <= 62
+    rc, col, rounds, confl, st = run_batch(ctx, b, gc.GC_SCHED_ASYNC, {"t1": 62, "t2": 4096, "window": 1})
+    assert rc == gc.GC_OK
+    assert st["conflicts"] == 0
+    for g in range(b.G):
+        sub = b.graph(g)
+        v0, v1 = int(b.vtx_off[g]), int(b.vtx_off[g + 1])
+        assert np.array_equal(col[v0:v1], O.ff(sub)), f"graph {g}"

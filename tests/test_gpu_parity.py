@@ -235,20 +235,24 @@ def test_checked_mode_passes_on_real_results(ctx):
             assert rc == gc.GC_OK and st["error_word"] == 0
 
 
-@pytest.mark.parametrize("make", [lambda: I.tri2d(64, 64), lambda: I.tri2d(50, 70, jitter=0.3, seed=9),
-                                  lambda: I.tri2d(300, 7), lambda: I.kuhn3d(12),
-                                  lambda: I.kuhn3d(9, permute=False), lambda: I.rgg(12000, 12.0, seed=2)],
-                         ids=["tri64", "tri_jit", "tri_narrow", "kuhn12", "kuhn9_nat", "rgg12k"])
-def test_ordered_round0_is_sequential_first_fit(ctx, make):
-    # A graph of at most 16384 vertices whose degrees all fit one thread is
-    # coloured in round 0 by one warp in id order, every lane seeing the final
-    # colours of all lower neighbours (in-chunk ones through the lane scan or
-    # the shuffle walk) and none of the higher ones: exactly Algorithm 1.
+@pytest.mark.parametrize("make,window", [
+    (lambda: I.tri2d(64, 64), 0), (lambda: I.tri2d(50, 70, jitter=0.3, seed=9), 0),
+    (lambda: I.tri2d(300, 7), 0), (lambda: I.kuhn3d(12), 0), (lambda: I.kuhn3d(9, permute=False), 0),
+    (lambda: I.rgg(12000, 12.0, seed=2), 0), (lambda: I.tri2d(300, 300, jitter=0.3, seed=5), 0),
+    (lambda: I.rgg(60000, 12.0, seed=3), 1), (lambda: I.kuhn3d(40), 1)],
+    ids=["tri64", "tri_jit", "tri_narrow", "kuhn12", "kuhn9_nat", "rgg12k", "tri300_jit", "rgg60k_w1",
+         "kuhn40_w1"])
+def test_ordered_round0_is_sequential_first_fit(ctx, make, window):
+    # An ordered graph (at most 16384 vertices, or naturally numbered, or any
+    # graph with window 1) whose degrees all fit one thread is coloured in
+    # round 0 in id order -- by one warp, or by a group of warps that wait for
+    # each other's lower ids -- every vertex seeing the final colours of all
+    # its lower neighbours and none of the higher ones: exactly Algorithm 1.
     g = make()
-    assert g.n <= 16384 and int(np.diff(g.row_ptr).max()) <= 62
+    assert int(np.diff(g.row_ptr).max()) <= 62
     ff = O.ff(g)
     for _ in range(3):
-        rc, col, st = run(ctx, g, gc.GC_SCHED_ASYNC, {"t1": 62, "t2": 4096})
+        rc, col, st = run(ctx, g, gc.GC_SCHED_ASYNC, {"t1": 62, "t2": 4096, "window": window})
         assert rc == gc.GC_OK
         assert np.array_equal(col, ff), f"first diff at {np.nonzero(col != ff)[0][:5]}"
         assert st["conflicts"] == 0 and st["rounds"] == 1
