@@ -164,15 +164,19 @@ typedef struct {
                                     entries) a single block finishes the
                                     colouring; 0 = 2048, -1 = never */
     int32_t window;              /* GC_SCHED_ASYNC round 0 (and the first
-                                    tentative phase of Algorithm 2): at most
-                                    this many tiles are coloured concurrently,
-                                    claimed in vertex order.  0 = automatic:
-                                    a graph of at most 16384 vertices, or one
-                                    whose edges mostly join nearby ids (a
-                                    naturally numbered mesh), is coloured in id
-                                    order by one warp (sequential First-Fit);
-                                    other graphs without limit.  1 = every
-                                    graph in id order; -1 = no ordering */
+                                    tentative phase of Algorithm 2): which
+                                    graphs are coloured strictly in id order
+                                    (each vertex once its lower neighbours are,
+                                    higher ones unread: sequential First-Fit).
+                                    0 = automatic: graphs of at most 16384
+                                    vertices, graphs whose edges mostly join
+                                    nearby ids (a naturally numbered mesh) and
+                                    graphs of at most 262144 vertices with no
+                                    vertex of degree > 62 or > t2; one warp
+                                    each, or a group of warps for a big one
+                                    without such vertices.  1 = every graph;
+                                    -1 = none (pure speculation); k > 1 = none,
+                                    and at most k tiles in flight */
 } gc_opts;
 
 typedef struct gc_ctx gc_ctx;

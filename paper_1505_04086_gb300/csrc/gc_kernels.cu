@@ -229,6 +229,9 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
+#ifndef GC_R0_SKIP_HIGHER
+#define GC_R0_SKIP_HIGHER 0  // tuning experiment: round-0 chunks read only lower neighbours
+#endif
 #ifndef GC_KEEPERS_MIN_DEG
 #define GC_KEEPERS_MIN_DEG 0  // GC_FF_KEEPERS applies to vertices of higher degree
 #endif
@@ -869,7 +872,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // With degree tiers the higher neighbours read here may be final
     // colours of an earlier tier, which no later round inspects: read them.
     const bool keepers = (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
-    const bool keep = keepers && deg > GC_KEEPERS_MIN_DEG;
+    const bool keep = (keepers && deg > GC_KEEPERS_MIN_DEG) || (GC_R0_SKIP_HIGHER && !RING && !(p.mode & GC_TIERS));
     int nread = 0;
     PT_BEGIN(t_g);
     if (thr) {
@@ -931,6 +934,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         mb += 8 + 8ll * nread + 4;
     }
     __syncwarp();
+    PT_BEGIN(t_mid);
     unsigned mm = midmask;
     while (mm) {
         const int src = __ffs(mm) - 1;
@@ -941,6 +945,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
         vertex_warp<true, false>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane, 0);
     }
+    PT_END(p.st, 5, t_mid);
     if (RING) {
         __syncwarp();
         if (v >= 0) {
@@ -1327,7 +1332,8 @@ __device__ bool chunk_pipe(const KParams &p, const E &ent, int32_t cb, int32_t v
 
 // Warp j of a group of K colours chunks j, j+K, j+2K, ... of graph g (ids
 // v0..v1-1) with chunk_pipe, staging each chunk's adjacency segment one
-// chunk ahead.  Only graphs without hubs or warp-path vertices are grouped.
+// chunk ahead.  Only graphs without hubs and without vertices of degree
+// above kT1Max are grouped: every lane colours its vertex alone, whatever t1.
 template <bool BATCH>
 __device__ __noinline__ void pipe_graph(const KParams &p, Shared &sh, int32_t g, long long v0, long long v1, int j,
                                         int K, int32_t *C, long long &mb, uint32_t &phase, int lane, int wid)
@@ -1575,8 +1581,10 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
+            PT_BEGIN(t_hub);
             bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
                      op == OP_TENT;  // round 0: hubs are kept for the first repair pass
+            PT_END(p.st, op == OP_TENT ? 4 : 12, t_hub);
             if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
                 atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
                 const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
@@ -1630,9 +1638,10 @@ __device__ long long block_sum(long long x, Shared &sh)
 
 // Block 0: decide which graphs are coloured in id order in round 0 of the
 // asynchronous mode (window 1: every graph; 0: graphs of at most
-// kOrderedSmall vertices and graphs whose sampled lower neighbours mostly lie
-// within kNearIds ids; else none), and how: a graph without hubs or
-// warp-path vertices whose chunks exceed the per-warp share of all ordered
+// kOrderedSmall vertices, graphs whose sampled lower neighbours mostly lie
+// within kNearIds ids, and graphs of at most kOrderedGroup vertices without
+// hubs or vertices of degree above kT1Max; else none), and how: a graph without hubs or vertices
+// of degree above kT1Max whose chunks exceed the per-warp share of all ordered
 // chunks gets a group of warps (pipe_graph; the groups together take at
 // most three quarters of the grid's warps), any other ordered graph one
 // warp.  Also numbers the chunks of the graphs that are not ordered
@@ -1649,15 +1658,17 @@ __device__ void plan_ordering(const KParams &p, Shared &sh)
     auto graph_n = [&](int g) -> long long {
         return BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
     };
+    auto groupable = [&](int g) -> bool {
+        return !tiers && p.gstat[g].hubs == 0 && p.gstat[g].wide == 0;
+    };
     auto is_ordered = [&](int g, long long ng) -> bool {
         const GraphStat &gs = p.gstat[g];
         // Small graphs are ordered too: coloured all at once they would be
-        // coloured almost simultaneously, whatever their numbering.
+        // coloured almost simultaneously, whatever their numbering.  So are
+        // graphs a warp group can take (up to kOrderedGroup vertices).
         return ng > 0 && (window == 1 || (window == 0 && (ng <= kOrderedSmall ||
-                                                          (gs.all_lower > 0 && 2 * gs.near_lower >= gs.all_lower))));
-    };
-    auto groupable = [&](int g) -> bool {
-        return !tiers && p.gstat[g].hubs == 0 && p.gstat[g].mids == 0;
+                                                          (gs.all_lower > 0 && 2 * gs.near_lower >= gs.all_lower) ||
+                                                          (ng <= kOrderedGroup && groupable(g)))));
     };
     // Ordered chunks in all, and the per-warp share of them.
     long long T = 0;
@@ -1776,8 +1787,8 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 hub = (end - beg) > p.t2;
                 midv = tiers && !hub && (end - beg) > p.t1;
                 if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
-                if (ASYNC && !hub && (end - beg) > p.t1 && __ldcg(&p.gstat[g].mids) == 0u)
-                    atomicOr(&p.gstat[g].mids, 1u);
+                if (ASYNC && !hub && (end - beg) > kT1Max && __ldcg(&p.gstat[g].wide) == 0u)
+                    atomicOr(&p.gstat[g].wide, 1u);
                 st_color<false>(p.cA + v, ASYNC ? 0 : 1);
                 if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
                 if (keep) p.mark[v] = 0;
@@ -1901,7 +1912,9 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             // those (every other vertex of U^0 = V is provably clean).
             if (ASYNC && !twop) {
                 const bool suspects = !snap;
+                PT_BEGIN(t_r0);
                 run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, window);
+                PT_END(p.st, 13, t_r0);
                 grid_sync(st, nbl);
                 if (blockIdx.x == 0 && threadIdx.x == 0 && it < kStamps) st->stamp[it] = global_timer();
                 if (ld_volatile(&st->error)) {
