@@ -29,6 +29,7 @@ constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entrie
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
+constexpr int kLocalitySampleEntries = 32;  // locality: entries read per sampled vertex
 constexpr int kOrderedGroup = 1 << 18;  // graphs this small without hubs or wide rows are ordered (round 0)
 constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order
 constexpr int kPipeMinChunks = 8;       // fewest chunks per warp of a group

@@ -38,8 +38,8 @@ namespace gc {
 #define PT_END(st, slot, var)
 #endif
 
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
-constexpr unsigned kBarrierMaxPolls = 1u << 26;
+constexpr unsigned long long kBarrierTimeoutNs = 10000000000ull;  // 10 s
+constexpr unsigned kBarrierMaxPolls = 1u << 28;
 
 // ------------------------------------------------------------------------
 // memory helpers
@@ -1840,7 +1840,9 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                         int64_t beg, end;
                         int32_t nbase;
                         row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, g);
-                        for (int64_t k = beg; k < end; ++k) {
+                        // at most kLocalitySampleEntries lower neighbours per sampled vertex
+                        const int64_t stop = min(end, beg + kLocalitySampleEntries);
+                        for (int64_t k = beg; k < stop; ++k) {
                             const int32_t u = nbase + __ldg(p.col_idx + k);
                             if (u >= (int32_t)vi) break;
                             ++all;
