@@ -157,6 +157,7 @@ class ClockSampler:
 MODES = {
     "rsoc_async": 0 | 2,        # GC_ALG_RSOC | GC_SCHED_ASYNC (headline)
     "rsoc_async_keepers": 0 | 2 | 512,  # ... | GC_FF_KEEPERS
+    "rsoc_async_tiers": 0 | 2 | 256,    # ... | GC_TIERS
     "rsoc_det": 0,              # GC_ALG_RSOC | GC_SCHED_DET
     "twophase_async": 1 | 2,    # GC_ALG_TWO_PHASE | GC_SCHED_ASYNC
     "twophase_det": 1,
@@ -261,8 +262,8 @@ def run_ours(args, ws, rank, local):
 
     extra = {}
     if not args.no_extra:
-        for name in ("rsoc_det", "twophase_async", "twophase_det"):
-            k = max(3, min(args.steps, 50))
+        for name in ("rsoc_det", "twophase_async", "twophase_det", "rsoc_async_tiers", "rsoc_async_keepers"):
+            k = max(3, min(args.steps, 20 if g.nnz > 50_000_000 else 50))
             r = time_mode(ctx, gc, torch, rp, ci, g, MODES[name], k, 3, flush, stream)
             tm = float(np.mean(r["step_ms"]))
             extra[name] = {"value": round(E / (tm / 1e3), 1), "ms_per_step": round(tm, 4),
@@ -308,7 +309,7 @@ def run_ours(args, ws, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded generator)",
-        "config": {"workload": f"{args.workload}_perm", "n": g.n, "edges": E, "nnz": g.nnz,
+        "config": {"workload": g.name, "n": g.n, "edges": E, "nnz": g.nnz,
                    "mode": "rsoc_async", "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas{ws}"},
         "p50_ms": round(pct(res["step_ms"], 50), 4), "p99_ms": round(pct(res["step_ms"], 99), 4),

@@ -232,6 +232,9 @@ constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in fl
 #ifndef GC_R0_SKIP_HIGHER
 #define GC_R0_SKIP_HIGHER 0  // tuning experiment: round-0 chunks read only lower neighbours
 #endif
+#ifndef GC_KEEPERS_ROUNDS
+#define GC_KEEPERS_ROUNDS 0x7fffffff  // tuning experiment: keepers choices in iterations <= this only
+#endif
 #ifndef GC_KEEPERS_MIN_DEG
 #define GC_KEEPERS_MIN_DEG 0  // GC_FF_KEEPERS applies to vertices of higher degree
 #endif
@@ -404,7 +407,7 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
                                               bool implicit, long long &mb, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     mb += (implicit ? 0 : 4) + 8;
     int t;
@@ -551,7 +554,7 @@ __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, in
                             int lane, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
@@ -723,7 +726,7 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
                              const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
