@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--mode", default="rsoc_async", help="batch/serve workloads: colouring mode")
+    ap.add_argument("--graphs", type=int, default=BATCH_G, help="batch workload: number of graphs")
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: default options, no autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline mode only")
     return ap.parse_args()
@@ -414,7 +416,7 @@ def run_batch(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    full = I.batch(BATCH_G, seed=I.SEED_BATCH)
+    full = I.batch(args.graphs, seed=I.SEED_BATCH)
     sizes = np.diff(full.vtx_off)
     mine = D.shard_graphs(sizes, rank, ws)
     b = I.Batch.from_graphs([full.graph(g) for g in mine], name="batch") if ws > 1 else full
@@ -434,9 +436,12 @@ def run_batch(args, ws, rank, local):
     mode = MODES[mode_name]
     steps = max(3, min(args.steps, 20))
     t_tune = time.perf_counter()
-    rc, tune = gc.gc_autotune_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, reps=1)
-    if rc != gc.GC_OK:
-        raise RuntimeError(gc.gc_strerror(rc))
+    if args.no_tune:
+        tune = {"best": None, "best_ms": 0.0, "default_ms": 0.0, "evaluated": 0}
+    else:
+        rc, tune = gc.gc_autotune_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, reps=1)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
     t_tune = time.perf_counter() - t_tune
     opts = tune["best"]
     plan = gc.Plan(local, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, rounds, confl, opts=opts)
@@ -488,7 +493,7 @@ def run_batch(args, ws, rank, local):
             "steps": steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic (seeded generator)",
-            "config": {"workload": f"batch{BATCH_G}_mesh_rgg_1k_256k", "graphs": BATCH_G,
+            "config": {"workload": f"batch{args.graphs}_mesh_rgg_1k_256k", "graphs": args.graphs,
                        "n": int(full.total_n), "edges": int(full.total_nnz // 2), "mode": mode_name,
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"graph-shards{ws}",
                        "launch": "CUDA graph replay (gc_plan_launch)"},

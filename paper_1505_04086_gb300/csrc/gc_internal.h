@@ -33,6 +33,7 @@ constexpr int kLocalitySampleEntries = 32;  // locality: entries read per sample
 constexpr int kOrderedGroup = 1 << 18;  // graphs this small without hubs or wide rows are ordered (round 0)
 constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order
 constexpr int kPipeMinChunks = 8;       // fewest chunks per warp of a group
+constexpr int kTargetSteps = 16;        // candidate chunk shares per grouped warp (x1.25 apart)
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 

@@ -229,15 +229,6 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
-#ifndef GC_R0_SKIP_HIGHER
-#define GC_R0_SKIP_HIGHER 0  // tuning experiment: round-0 chunks read only lower neighbours
-#endif
-#ifndef GC_KEEPERS_ROUNDS
-#define GC_KEEPERS_ROUNDS 0x7fffffff  // tuning experiment: keepers choices in iterations <= this only
-#endif
-#ifndef GC_KEEPERS_MIN_DEG
-#define GC_KEEPERS_MIN_DEG 0  // GC_FF_KEEPERS applies to vertices of higher degree
-#endif
 #ifndef GC_PASS_INLINE
 #define GC_PASS_INLINE __forceinline__
 #endif
@@ -407,7 +398,7 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
                                               bool implicit, long long &mb, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS);
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     mb += (implicit ? 0 : 4) + 8;
     int t;
@@ -554,7 +545,7 @@ __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, in
                             int lane, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS);
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
@@ -726,7 +717,7 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
                              const int32_t *R, int32_t *W, bool implicit, long long &mb, Shared &sh, int it)
 {
     const int deg = (int)(end - beg);
-    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) && deg > GC_KEEPERS_MIN_DEG && it <= GC_KEEPERS_ROUNDS;
+    const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS);
     const int32_t vmax = keep ? v - 1 : INT32_MAX;
     long long add = (implicit ? 0 : 4) + 8;
     bool d = false;
@@ -875,7 +866,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // With degree tiers the higher neighbours read here may be final
     // colours of an earlier tier, which no later round inspects: read them.
     const bool keepers = (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
-    const bool keep = (keepers && deg > GC_KEEPERS_MIN_DEG) || (GC_R0_SKIP_HIGHER && !RING && !(p.mode & GC_TIERS));
+    const bool keep = keepers;
     int nread = 0;
     PT_BEGIN(t_g);
     if (thr) {
@@ -1650,14 +1641,14 @@ __device__ long long block_sum(long long x, Shared &sh)
 // warp.  Also numbers the chunks of the graphs that are not ordered
 // (prefix sums in uofs).
 template <bool BATCH>
-__device__ void plan_ordering(const KParams &p, Shared &sh)
+__device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
 {
     DevState *st = p.st;
     const int window = p.window;
     const bool tiers = (p.mode & GC_TIERS) != 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const long long warps = (long long)gridDim.x * kWarps;
-    const long long budget = min(warps, (long long)p.pitems_cap) * 3 / 4;
+    const long long budget = min(warps, (long long)p.pitems_cap) * 7 / 8;
     auto graph_n = [&](int g) -> long long {
         return BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
     };
@@ -1673,7 +1664,7 @@ __device__ void plan_ordering(const KParams &p, Shared &sh)
                                                           (gs.all_lower > 0 && 2 * gs.near_lower >= gs.all_lower) ||
                                                           (ng <= kOrderedGroup && groupable(g)))));
     };
-    // Ordered chunks in all, and the per-warp share of them.
+    // Ordered chunks in all.
     long long T = 0;
     for (int g0 = 0; g0 < p.G; g0 += kBlock) {
         const int g = g0 + threadIdx.x;
@@ -1684,29 +1675,74 @@ __device__ void plan_ordering(const KParams &p, Shared &sh)
         }
         T += block_sum(c, sh);
     }
-    long long target = max((T + warps - 1) / max(warps, 1ll), (long long)kPipeMinChunks);
+    // The chunks per grouped warp, `target`: the smallest of kTargetSteps
+    // candidates (from the even share of all ordered chunks upwards, x1.25
+    // each) at which the groups fit the budget and the graphs left to single
+    // warps fit on the remaining warps at `target` chunks each.
+    long long cand[kTargetSteps];
+    cand[0] = max((T + warps - 1) / max(warps, 1ll), (long long)kPipeMinChunks);
+    for (int i = 1; i < kTargetSteps; ++i) cand[i] = cand[i - 1] + cand[i - 1] / 4 + 1;
+    long long *acc = reinterpret_cast<long long *>(sh.hub_bm);  // [2 * kTargetSteps], block-local scratch
+    for (int i = threadIdx.x; i < 2 * kTargetSteps; i += kBlock) acc[i] = 0;
+    __syncthreads();
+    {
+        long long wg[kTargetSteps], single[kTargetSteps];
+#pragma unroll
+        for (int i = 0; i < kTargetSteps; ++i) wg[i] = single[i] = 0;
+        for (int g = threadIdx.x; g < p.G; g += kBlock) {
+            const long long ng = graph_n(g);
+            if (!is_ordered(g, ng)) continue;
+            const long long c = (ng + 31) / 32;
+            const bool gr = groupable(g);
+#pragma unroll
+            for (int i = 0; i < kTargetSteps; ++i) {
+                if (gr && c > cand[i]) wg[i] += min((c + cand[i] - 1) / cand[i], (long long)kPipeMaxK);
+                else single[i] += c;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kTargetSteps; ++i) {
+            if (wg[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&acc[2 * i]), (unsigned long long)wg[i]);
+            if (single[i]) atomicAdd(reinterpret_cast<unsigned long long *>(&acc[2 * i + 1]), (unsigned long long)single[i]);
+        }
+    }
+    __syncthreads();
+    long long target = cand[kTargetSteps - 1];
+    for (int i = 0; i < kTargetSteps; ++i) {
+        const long long wgi = acc[2 * i], si = acc[2 * i + 1];
+        if (wgi <= budget && si <= cand[i] * (warps - wgi)) {
+            target = cand[i];
+            break;
+        }
+    }
+    __syncthreads();
     auto group_of = [&](long long chunks) -> int {
         return chunks > target ? (int)min((chunks + target - 1) / target, (long long)kPipeMaxK) : 1;
     };
-    for (;;) {  // widen the share until the groups fit the budget
-        long long need = 0;
-        for (int g0 = 0; g0 < p.G; g0 += kBlock) {
-            const int g = g0 + threadIdx.x;
-            long long k = 0;
-            if (g < p.G) {
-                const long long ng = graph_n(g);
-                if (is_ordered(g, ng) && groupable(g)) {
-                    const int K = group_of((ng + 31) / 32);
-                    if (K > 1) k = K;
-                }
-            }
-            need += block_sum(k, sh);
-        }
-        if (need <= budget || target > (1ll << 40)) break;
-        target *= 2;
+    // Graphs left to single warps are listed largest first (by powers of two
+    // of their chunk counts), so that the longest start first.
+    int *bucket = reinterpret_cast<int *>(sh.hub_bm);  // [64]: counts, then fill positions
+    for (int i = threadIdx.x; i < 64; i += kBlock) bucket[i] = 0;
+    __syncthreads();
+    auto bucket_of = [&](long long chunks) -> int { return 63 - __clzll((unsigned long long)chunks | 1ull); };
+    for (int g = threadIdx.x; g < p.G; g += kBlock) {
+        const long long ng = graph_n(g);
+        if (is_ordered(g, ng) && (!groupable(g) || group_of((ng + 31) / 32) == 1))
+            atomicAdd(&bucket[bucket_of((ng + 31) / 32)], 1);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 31; b >= 0; --b) {  // largest first
+            const int c = bucket[b];
+            bucket[32 + b] = run;
+            run += c;
+        }
+        st->n_ordered = run;
+    }
+    __syncthreads();
     long long carry = 0;
-    long long *warp_tot = reinterpret_cast<long long *>(sh.hub_bm);  // block-local scratch
+    long long *warp_tot = reinterpret_cast<long long *>(sh.hub_bm) + 32;  // block-local scratch after bucket[]
     for (int g0 = 0; g0 < p.G; g0 += kBlock) {
         const int g = g0 + threadIdx.x;
         long long chunks = 0;
@@ -1722,7 +1758,7 @@ __device__ void plan_ordering(const KParams &p, Shared &sh)
                 for (int j = 0; j < K; ++j)
                     p.pitems[base + j] = ((long long)g << 20) | ((long long)j << 10) | (long long)(K - 1);
             } else if (ord) {
-                p.olist[atomicAdd(&st->n_ordered, 1)] = g;
+                p.olist[atomicAdd(&bucket[32 + bucket_of((ng + 31) / 32)], 1)] = g;
             } else {
                 chunks = (ng + 31) / 32;
             }
