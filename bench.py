@@ -507,7 +507,9 @@ def run_batch(args, ws, rank, local):
             "rounds": st["rounds"], "conflicts": st["conflicts"],
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
-                         "traffic": None, "kernel": "gc::color_kernel<async,batch>"},
+                         "traffic": recorded_traffic(f"batch{args.graphs}", mode_name),
+                         "kernel": "gc::color_kernel<async,batch>",
+                         "algorithmic_bytes_per_launch": int(np.mean(mbs)), "kernel_ms": round(float(np.mean(kms)), 4)},
             "gpu_launches": 4 * steps, "clocks": clocks}  # lut, colour, stats, popcount
     plan.close()
     ctx.close()
