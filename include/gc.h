@@ -315,6 +315,11 @@ typedef struct {
 int gc_autotune_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, int32_t reps, int32_t *colors_out,
                       gc_tune_result *result);
 
+/* As gc_autotune_batch for one graph (device pointers; gc_color_async
+ * semantics): colors_out (n entries) receives the colourings. */
+int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
+                int32_t *colors_out, gc_tune_result *result);
+
 /* ---- serving: continuous batching of colouring requests ------------------ */
 
 /*

@@ -142,8 +142,6 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     if ((e = cudaMemsetAsync(c->gstat.p, 0, (size_t)std::max(p.G, 1) * sizeof(gc::GraphStat), s)) != cudaSuccess)
         return cuda_status(e);
     const bool stats = !(mode & GC_NO_COLOR_STATS);
-    if (stats && (e = cudaMemsetAsync(c->bitmap.p, 0, gc::kStatBitmapWords * sizeof(uint32_t), s)) != cudaSuccess)
-        return cuda_status(e);
     if (batch && (e = gc::launch_build_lut(p.vtx_off, p.G, p.n, c->lut.as<int32_t>(), s)) != cudaSuccess)
         return cuda_status(e);
     if ((mode & GC_VALIDATE) && (e = gc::launch_validate(p, batch, aux_grid, s)) != cudaSuccess)
@@ -158,10 +156,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
         return cuda_status(e);
     if ((e = cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_status(e);
-    c->last.rounds_copied = 256;
-    if ((e = cudaMemcpyAsync(c->rs_host, c->round_sizes.p, 256 * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
-        cudaSuccess)
-        return cuda_status(e);
+    c->last.rounds_copied = gc::kStamps;  // DevState::round_head
     if ((e = record(c, c->ev_done, s)) != cudaSuccess) return cuda_status(e);
     c->last.stats = stats;
     return GC_OK;
@@ -326,6 +321,9 @@ int gc_ctx_create(gc_ctx **out, int device)
                         !c->bitmap.reserve(gc::kStatBitmapWords * sizeof(uint32_t)) ||
                         !c->round_sizes.reserve(kRoundSizesDev * sizeof(int32_t))))
         rc = GC_ERR_OOM;
+    // the colour-statistics kernel leaves the bitmap zero after every use
+    if (rc == GC_OK && cudaMemset(c->bitmap.p, 0, gc::kStatBitmapWords * sizeof(uint32_t)) != cudaSuccess)
+        rc = GC_ERR_CUDA;
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             if (rc == GC_OK && c->occ[a][b] < 1) rc = GC_ERR_CUDA;
@@ -438,14 +436,16 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
         if (rs && cap > 0) {
             int32_t k = std::min<int32_t>(std::min<int32_t>(s.rounds, cap), kRoundSizesDev);
             if (k > c->last.rounds_copied) {
-                // more than the prefetched prefix: fetch synchronously
+                // more than the head copied back with the state: fetch synchronously
                 if (cudaMemcpy(c->rs_host, c->round_sizes.p, (size_t)k * sizeof(int32_t),
                                cudaMemcpyDeviceToHost) != cudaSuccess) {
                     cudaGetLastError();
                     k = 0;
                 }
+                memcpy(rs, c->rs_host, (size_t)std::max(k, 0) * sizeof(int32_t));
+            } else {
+                memcpy(rs, c->st_host->round_head, (size_t)std::max(k, 0) * sizeof(int32_t));
             }
-            memcpy(rs, c->rs_host, (size_t)std::max(k, 0) * sizeof(int32_t));
         }
         s.round_sizes = rs;
         s.round_sizes_cap = cap;

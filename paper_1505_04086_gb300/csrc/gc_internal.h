@@ -95,6 +95,8 @@ struct DevState {
     int window;                      // number of graphs coloured in id order in round 0
     unsigned long long t_start;      // globaltimer at kernel start (ns)
     unsigned long long stamp[kStamps];  // [0]: end of round 0, [k]: end of iteration k
+    int round_head[kStamps];         // |L| of iterations 1..kStamps (copied back with the state)
+    unsigned int stats_done;         // colour-statistics blocks finished
 };
 
 struct KParams {

@@ -235,14 +235,26 @@ constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in fl
 
 // Adjacency entry k (a global CSR index) of the row being processed: read
 // from col_idx, or from the warp's staged copy of the chunk's segment.
+// row(beg) gives a cursor over the entries from beg on, indexed with 32-bit
+// offsets (rows hold at most 2^31 entries).
 struct GlobalEnts {
     const int32_t *col;
     __device__ __forceinline__ int32_t operator()(int64_t k) const { return __ldg(col + k); }
+    struct Row {
+        const int32_t *p;
+        __device__ __forceinline__ int32_t operator[](int i) const { return __ldg(p + i); }
+    };
+    __device__ __forceinline__ Row row(int64_t beg) const { return Row{col + beg}; }
 };
 struct StagedEnts {
     const int32_t *buf;        // shared memory: entry k is buf[k - off]
     int64_t off;
     __device__ __forceinline__ int32_t operator()(int64_t k) const { return buf[k - off]; }
+    struct Row {
+        const int32_t *p;
+        __device__ __forceinline__ int32_t operator[](int i) const { return p[i]; }
+    };
+    __device__ __forceinline__ Row row(int64_t beg) const { return Row{buf + (beg - off)}; }
 };
 
 // Smallest colour >= 1 not held by a neighbour u <= vmax (Algorithm 1 body;
@@ -255,13 +267,14 @@ __device__ __forceinline__ int ff_thread(const E &ent, int64_t beg, int deg, int
 {
     unsigned long long mask = 0;
     t = 0;
+    const auto row = ent.row(beg);
     for (int i = 0; i < deg; i += kUnroll) {
         int u[kUnroll];
         bool take[kUnroll];
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) {
             const bool in = i + q < deg;
-            u[q] = in ? nbase + ent(beg + i + q) : 0;
+            u[q] = in ? nbase + row[i + q] : 0;
             take[q] = in && u[q] <= vmax;
         }
         int c[kUnroll];
@@ -336,13 +349,14 @@ __device__ __forceinline__ void push_clashes_thread(const KParams &p, const E &e
                                                     int64_t end, int32_t nbase, const int32_t *R, int k, int it)
 {
     const int deg = (int)(end - beg);
+    const auto row = ent.row(beg);
     for (int i = 0; i < deg; i += kUnroll) {
         int u[kUnroll];
         bool side[kUnroll];
 #pragma unroll
         for (int q = 0; q < kUnroll; ++q) {
             const bool in = i + q < deg;
-            u[q] = in ? nbase + ent(end - 1 - (i + q)) : 0;
+            u[q] = in ? nbase + row[deg - 1 - (i + q)] : 0;
             side[q] = in && u[q] > v;
         }
         int c[kUnroll];
@@ -364,6 +378,7 @@ __device__ __forceinline__ bool detect_thread(const E &ent, int tie, int32_t v, 
     const int deg = (int)(end - beg);
     bool def = false;
     t = 0;
+    const auto row = ent.row(beg);
     for (int i = 0; i < deg; i += kUnroll) {
         int u[kUnroll];
         bool side[kUnroll];
@@ -371,8 +386,7 @@ __device__ __forceinline__ bool detect_thread(const E &ent, int tie, int32_t v, 
         for (int q = 0; q < kUnroll; ++q) {
             const int ii = i + q;
             const bool in = ii < deg;
-            const int64_t k = (tie == TIE_HIGHER) ? end - 1 - ii : beg + ii;
-            u[q] = in ? nbase + ent(k) : 0;
+            u[q] = in ? nbase + row[(tie == TIE_HIGHER) ? deg - 1 - ii : ii] : 0;
             side[q] = in && on_tie_side(tie, u[q], v);
         }
         int c[kUnroll];
@@ -500,7 +514,10 @@ __device__ void push_clashes_warp(const KParams &p, int32_t v, int64_t beg, int6
 }
 
 constexpr int kWarpUnroll = 4;   // entries per lane in flight (warp path)
-constexpr int kBlockUnroll = 4;  // entries per thread in flight (block path)
+#ifndef GC_BLOCK_UNROLL
+#define GC_BLOCK_UNROLL 4
+#endif
+constexpr int kBlockUnroll = GC_BLOCK_UNROLL;  // entries per thread in flight (block path)
 
 template <bool ASYNC>
 __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
@@ -700,10 +717,11 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
                 ++t;
                 def |= (c[q] == cv);
             }
-        const int more = __syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side[kBlockUnroll - 1] : 0);
-        const int any_def = __syncthreads_or((int)def);
-        if (tie != TIE_NONE && !more) break;
-        if (any_def && stop_early) break;
+        // one barrier: bit 0 = the tie side goes on, bit 1 = a conflict was seen
+        const int flags = __syncthreads_or(((threadIdx.x == kBlock - 1 && side[kBlockUnroll - 1]) ? 1 : 0) |
+                                           (def ? 2 : 0));
+        if (tie != TIE_NONE && !(flags & 1)) break;
+        if ((flags & 2) && stop_early) break;
     }
     if (t) atomicAdd(&sh.tcount, t);
     const int any = __syncthreads_or((int)def);
@@ -866,16 +884,19 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // With degree tiers the higher neighbours read here may be final
     // colours of an earlier tier, which no later round inspects: read them.
     const bool keepers = (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
-    const bool keep = keepers;
+    // An ordered graph whose higher ids are all uncoloured (skip_higher)
+    // gains nothing from the part of a row above v either.
+    const bool keep = keepers || (RING && skip_higher);
     int nread = 0;
     PT_BEGIN(t_g);
     if (thr) {
+        const auto row = ent.row(beg);
         for (int i = 0; i < deg; i += kUnroll) {
             int u[kUnroll];
             bool outside[kUnroll];
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
-                u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
+                u[q] = (i + q < deg) ? nbase + row[i + q] : -1;
                 if (keep && u[q] > v) u[q] = -1;
                 nread += u[q] >= 0;
                 const uint32_t d = (uint32_t)(u[q] - cb32);  // in-chunk offset (wraps when outside)
@@ -1259,11 +1280,12 @@ __device__ bool chunk_pipe(const KParams &p, const E &ent, int32_t cb, int32_t v
         bool pend = false;
         int nlo = 0;
         if (todo) {
+            const auto row = ent.row(beg);
             for (int i = 0; i < deg; i += kUnroll) {
                 int u[kUnroll];
 #pragma unroll
                 for (int q = 0; q < kUnroll; ++q) {
-                    u[q] = (i + q < deg) ? nbase + ent(beg + i + q) : -1;
+                    u[q] = (i + q < deg) ? nbase + row[i + q] : -1;
                     if (u[q] > v) u[q] = -1;  // higher neighbours are not looked at
                 }
                 int c[kUnroll];
@@ -2005,6 +2027,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                     st->rounds = it;
                     st->conflicts += (unsigned long long)tot;
                     if (p.round_sizes && it - 1 < p.round_sizes_cap) p.round_sizes[it - 1] = tot;
+                    if (it - 1 < kStamps) st->round_head[it - 1] = tot;
                 }
                 if (snap) {
                     int32_t *t = R;
@@ -2051,9 +2074,13 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 // auxiliary kernels
 // ------------------------------------------------------------------------
 
-// Largest colour and presence bitmap of colours (for the distinct count).
+// Largest colour and presence bitmap of colours; the last block to finish
+// counts the distinct colours and clears the bitmap for the next call (it
+// must be zero on entry).
 __global__ void color_stats_kernel(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
 {
+    __shared__ int acc;
+    __shared__ bool last;
     int mx = 0;
     unsigned long long low = 0;  // colours 0..63, OR-reduced per warp
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -2072,26 +2099,30 @@ __global__ void color_stats_kernel(const int32_t *c, int32_t n, DevState *st, ui
         if (low & 0xffffffffull) atomicOr(&bitmap[0], (uint32_t)low);
         if (low >> 32) atomicOr(&bitmap[1], (uint32_t)(low >> 32));
     }
-}
-
-__global__ void popcount_kernel(const uint32_t *bitmap, DevState *st)
-{
-    __shared__ int acc;
-    if (threadIdx.x == 0) acc = 0;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
+        acc = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     int s = 0;
-    for (int w = threadIdx.x; w < kStatBitmapWords; w += blockDim.x) {
-        uint32_t x = bitmap[w];
-        if (w == 0) x &= ~1u;  // colour 0 is not a colour
-        s += __popc(x);
+    uint4 *bm4 = reinterpret_cast<uint4 *>(bitmap);
+    constexpr int kWords4 = kStatBitmapWords / 4;
+#pragma unroll 8
+    for (int w = threadIdx.x; w < kWords4; w += blockDim.x) {  // independent 16-byte loads in flight
+        uint4 x = __ldcg(bm4 + w);
+        if (x.x | x.y | x.z | x.w) bm4[w] = make_uint4(0u, 0u, 0u, 0u);
+        if (w == 0) x.x &= ~1u;  // colour 0 is not a colour
+        s += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
     }
     atomicAdd(&acc, s);
     __syncthreads();
     if (threadIdx.x == 0) st->distinct = acc;
 }
 
-// Input well-formedness: row pointers, range, no self-loop, strictly
-// increasing rows and a mirror entry for every entry.
 template <bool BATCH>
 __global__ void validate_kernel(KParams p)
 {
@@ -2234,9 +2265,6 @@ cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, u
                                cudaStream_t s)
 {
     color_stats_kernel<<<grid, 256, 0, s>>>(colors, n, st, bitmap);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    popcount_kernel<<<1, 1024, 0, s>>>(bitmap, st);
     return cudaGetLastError();
 }
 

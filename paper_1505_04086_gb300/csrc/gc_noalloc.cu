@@ -193,11 +193,10 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     const int aux_grid = (int)(useful < (long long)d->num_sms * 8 ? (useful > 0 ? useful : 1) : d->num_sms * 8);
     const bool stats = !(mode & GC_NO_COLOR_STATS);
 
-    // Clear what must start at zero: the launch state and the colour bitmap.
+    // Clear what must start at zero: the launch state (the colour bitmap is
+    // zero from load time and left zero by every statistics pass).
     cudaError_t e = cudaMemsetAsync(p.st, 0, sizeof(gc::DevState), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p.gstat, 0, sizeof(gc::GraphStat), st);
-    if (e == cudaSuccess && stats)
-        e = cudaMemsetAsync(base + kOffBitmap, 0, gc::kStatBitmapWords * sizeof(uint32_t), st);
     if (e == cudaSuccess && (mode & GC_VALIDATE)) e = gc::launch_validate(p, false, aux_grid, st);
     if (e == cudaSuccess) e = gc::launch_color(p, async, false, (int)grid, st);
     if (e == cudaSuccess && (mode & GC_CHECKED)) e = gc::launch_check(p, false, aux_grid, st);

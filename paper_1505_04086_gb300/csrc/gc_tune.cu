@@ -1,6 +1,6 @@
 // Batch plans (one gc_color_batch call captured into a CUDA graph and
-// replayed) and the option autotuner for batches: the extern "C" entry
-// points gc_plan_* and gc_autotune_batch of include/gc.h.
+// replayed) and the option autotuner: the extern "C" entry points gc_plan_*,
+// gc_autotune_batch and gc_autotune of include/gc.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +44,79 @@ int run_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o, int
 {
     return gc::color_batch_impl(c, b->G, b->total_n, b->total_nnz, b->vtx_off, b->edge_off, nullptr, b->row_ptr,
                                 b->col_idx, mode, o, colors_out, nullptr, nullptr, s);
+}
+
+// Coordinate descent over the option knobs (see gc_autotune_batch in gc.h):
+// run(o) enqueues one colouring with options o on the legacy stream.
+template <class Run>
+int tune(gc_ctx *ctx, int reps, gc_tune_result *out, Run run)
+{
+    memset(out, 0, sizeof *out);
+    // Device time of one option set: median over reps runs.
+    auto measure = [&](const gc_opts &o, float &ms) -> int {
+        std::vector<float> t;
+        for (int r = 0; r < reps; ++r) {
+            int rc = run(o);
+            gc_stats st;
+            memset(&st, 0, sizeof st);
+            if (rc == GC_OK) rc = gc_ctx_stats(ctx, &st);
+            if (rc != GC_OK) return rc;
+            t.push_back(st.elapsed_ms);
+        }
+        std::sort(t.begin(), t.end());
+        ms = t[t.size() / 2];
+        ++out->evaluated;
+        return GC_OK;
+    };
+    // The knobs (only those that leave the method's result alone: window,
+    // which decides which graphs are coloured in id order, changes colour
+    // counts and is not tuned), each with its candidate values.
+    struct Knob {
+        int32_t gc_opts::*field;
+        std::vector<int32_t> values;
+    };
+    const std::vector<Knob> knobs = {
+        {&gc_opts::t1, {8, 16, 24, 32, 48, 62}},
+        {&gc_opts::t2, {128, 256, 512, 1024, 2048, 4096}},
+        {&gc_opts::tile, {32, 64, 128, 256, 512}},
+        {&gc_opts::blocks_per_sm, {1, 2, 0}},
+        {&gc_opts::tail, {-1, 256, 2048, 8192}},
+    };
+    gc_opts best;  // the library defaults, spelled out
+    memset(&best, 0, sizeof best);
+    best.t1 = 32;
+    best.t2 = 2048;
+    best.tile = 64;
+    best.tail = 2048;
+    float best_ms = 0.f;
+    int rc = measure(best, best_ms);
+    if (rc != GC_OK) return rc;
+    out->default_ms = best_ms;
+    // Coordinate descent from the defaults: two sweeps over the knobs, each
+    // knob set to its fastest value with the others held.
+    for (int sweep = 0; sweep < 2; ++sweep) {
+        bool moved = false;
+        for (const Knob &k : knobs) {
+            const int32_t cur = best.*(k.field);
+            for (int32_t v : k.values) {
+                if (v == cur) continue;
+                gc_opts o = best;
+                o.*(k.field) = v;
+                if (o.t1 > o.t2) continue;  // thread bin above the warp bin
+                float ms = 0.f;
+                if ((rc = measure(o, ms)) != GC_OK) return rc;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = o;
+                    moved = true;
+                }
+            }
+        }
+        if (!moved) break;
+    }
+    out->best = best;
+    out->best_ms = best_ms;
+    return GC_OK;
 }
 
 }  // namespace
@@ -139,72 +212,17 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t rep
     if (!ctx || !out || !batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
         reps > 64)
         return GC_ERR_ARG;
-    memset(out, 0, sizeof *out);
-    // Device time of one option set: median over reps runs.
-    auto measure = [&](const gc_opts &o, float &ms) -> int {
-        std::vector<float> t;
-        for (int r = 0; r < reps; ++r) {
-            int rc = run_batch(ctx, b, mode, &o, colors_out, nullptr);
-            gc_stats st;
-            memset(&st, 0, sizeof st);
-            if (rc == GC_OK) rc = gc_ctx_stats(ctx, &st);
-            if (rc != GC_OK) return rc;
-            t.push_back(st.elapsed_ms);
-        }
-        std::sort(t.begin(), t.end());
-        ms = t[t.size() / 2];
-        ++out->evaluated;
-        return GC_OK;
-    };
-    // The knobs (only those that leave the method's result alone: window,
-    // which decides which graphs are coloured in id order, changes colour
-    // counts and is not tuned), each with its candidate values.
-    struct Knob {
-        int32_t gc_opts::*field;
-        std::vector<int32_t> values;
-    };
-    std::vector<Knob> knobs = {
-        {&gc_opts::t1, {8, 16, 24, 32, 48, 62}},
-        {&gc_opts::t2, {128, 256, 512, 1024, 2048, 4096}},
-        {&gc_opts::tile, {32, 64, 128, 256, 512}},
-        {&gc_opts::blocks_per_sm, {1, 2, 0}},
-        {&gc_opts::tail, {-1, 256, 2048, 8192}},
-    };
-    gc_opts best;  // the library defaults, spelled out
-    memset(&best, 0, sizeof best);
-    best.t1 = 32;
-    best.t2 = 2048;
-    best.tile = 64;
-    best.tail = 2048;
-    float best_ms = 0.f;
-    int rc = measure(best, best_ms);
-    if (rc != GC_OK) return rc;
-    out->default_ms = best_ms;
-    // Coordinate descent from the defaults: two sweeps over the knobs, each
-    // knob set to its fastest value with the others held.
-    for (int sweep = 0; sweep < 2; ++sweep) {
-        bool moved = false;
-        for (const Knob &k : knobs) {
-            const int32_t cur = best.*(k.field);
-            for (int32_t v : k.values) {
-                if (v == cur) continue;
-                gc_opts o = best;
-                o.*(k.field) = v;
-                if (o.t1 > o.t2) continue;  // thread bin above the warp bin
-                float ms = 0.f;
-                if ((rc = measure(o, ms)) != GC_OK) return rc;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = o;
-                    moved = true;
-                }
-            }
-        }
-        if (!moved) break;
-    }
-    out->best = best;
-    out->best_ms = best_ms;
-    return GC_OK;
+    return tune(ctx, reps, out, [&](const gc_opts &o) { return run_batch(ctx, b, mode, &o, colors_out, nullptr); });
+}
+
+int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
+                int32_t *colors_out, gc_tune_result *out)
+{
+    if (!ctx || !out || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || !gc::mode_ok(mode) ||
+        (n > 0 && (!csr->row_ptr || !colors_out)) || (nnz > 0 && !csr->col_idx) || reps < 1 || reps > 64)
+        return GC_ERR_ARG;
+    return tune(ctx, reps, out,
+                [&](const gc_opts &o) { return gc_color_async(ctx, csr, n, nnz, mode, &o, colors_out, nullptr); });
 }
 
 }  // extern "C"

@@ -116,6 +116,8 @@ _SIGS = {
     "gc_plan_destroy": (None, [_P]),
     "gc_autotune_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32, ctypes.c_int32, _P,
                                          ctypes.POINTER(gc_tune_result)]),
+    "gc_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_int32, _P, ctypes.POINTER(gc_tune_result)]),
     "gc_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts)]),
     "gc_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
@@ -309,6 +311,17 @@ def gc_autotune_batch(ctx: int, G: int, total_n: int, total_nnz: int, vtx_off, e
     r = gc_tune_result()
     rc = load().gc_autotune_batch(ctypes.c_void_p(ctx), ctypes.byref(b), int(mode), int(reps),
                                   _ptr(colors_out), ctypes.byref(r))
+    return int(rc), {"best": opts_dict(r.best), "best_ms": float(r.best_ms),
+                     "default_ms": float(r.default_ms), "evaluated": int(r.evaluated)}
+
+
+def gc_autotune(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, reps: int = 3):
+    """Time option sets on one graph; returns (status, result dict as
+    gc_autotune_batch)."""
+    csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
+    r = gc_tune_result()
+    rc = load().gc_autotune(ctypes.c_void_p(ctx), ctypes.byref(csr), int(n), int(nnz), int(mode), int(reps),
+                            _ptr(colors_out), ctypes.byref(r))
     return int(rc), {"best": opts_dict(r.best), "best_ms": float(r.best_ms),
                      "default_ms": float(r.default_ms), "evaluated": int(r.evaluated)}
 

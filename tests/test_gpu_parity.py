@@ -256,3 +256,15 @@ def test_ordered_round0_is_sequential_first_fit(ctx, make, window):
         assert rc == gc.GC_OK
         assert np.array_equal(col, ff), f"first diff at {np.nonzero(col != ff)[0][:5]}"
         assert st["conflicts"] == 0 and st["rounds"] == 1
+
+
+@pytest.mark.parametrize("window", [-1, 2, 16])
+@pytest.mark.parametrize("alg", [gc.GC_ALG_RSOC, gc.GC_ALG_TWO_PHASE], ids=["rsoc", "twophase"])
+def test_async_window_modes_valid(ctx, window, alg):
+    # window -1: pure speculation (nothing ordered); k > 1: at most k tiles
+    # of round 0 in flight, claimed in vertex order.
+    for g in (I.kuhn3d(24), I.tri2d(100, 100, jitter=0.3, seed=4), I.rmat(12), I.rgg(20000, 12.0, seed=6)):
+        rc, col, st = run(ctx, g, alg | gc.GC_SCHED_ASYNC, {"window": window})
+        assert rc == gc.GC_OK, gc.gc_strerror(rc)
+        assert O.check(g, col)[0] == 0, g.name
+        assert st["colors"] == int(col.max())

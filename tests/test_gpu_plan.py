@@ -91,3 +91,18 @@ def test_autotune_picks_a_valid_faster_or_equal_option_set(mode):
             v0, v1 = int(b.vtx_off[g]), int(b.vtx_off[g + 1])
             assert np.array_equal(c[v0:v1], O.rsoc_det(b.graph(g)).colors)
     ctx.close()
+
+
+def test_autotune_single_graph():
+    g = I.kuhn3d(20)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    col = torch.zeros(g.n, dtype=torch.int32, device="cuda:0")
+    ctx = gc.Context(0)
+    rc, res = gc.gc_autotune(ctx.handle, rp, ci, g.n, g.nnz, gc.GC_ALG_RSOC, col, reps=1)
+    assert rc == gc.GC_OK
+    assert res["evaluated"] > 10 and 0 < res["best_ms"] <= res["default_ms"]
+    out, rc, st = ctx.color(rp, ci, gc.GC_ALG_RSOC, opts=res["best"])
+    assert rc == gc.GC_OK
+    assert np.array_equal(out.cpu().numpy(), O.rsoc_det(g).colors)
+    ctx.close()
