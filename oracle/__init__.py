@@ -61,6 +61,8 @@ def _load():
             lib.oracle_chi.argtypes = [i32, P, P]
             lib.oracle_csr_check.restype = i64
             lib.oracle_csr_check.argtypes = [i32, i64, P, P]
+            lib.oracle_classes.restype = i64
+            lib.oracle_classes.argtypes = [i32, P, i32, P, P]
             _lib = lib
         return _lib
 
@@ -153,3 +155,20 @@ def csr_check(g) -> int:
     first offending vertex."""
     rp, ci = _arrays(g)
     return int(_load().oracle_csr_check(g.n, g.nnz, rp.ctypes.data, ci.ctypes.data))
+
+
+def classes(colors, k: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """Colour classes of a colouring (stable counting sort by colour):
+    (ptr[k+2], verts[n]); the vertices of colour c are verts[ptr[c]:ptr[c+1]]
+    in increasing id."""
+    c = np.ascontiguousarray(colors, dtype=np.int32)
+    n = int(c.size)
+    if k is None:
+        k = int(c.max()) if n else 0
+    ptr = np.zeros(k + 2, np.int32)
+    verts = np.zeros(max(n, 1), np.int32)
+    cc = c if n else np.zeros(1, np.int32)
+    r = _load().oracle_classes(n, cc.ctypes.data, int(k), ptr.ctypes.data, verts.ctypes.data)
+    if r != 0:
+        raise ValueError(f"colour out of 1..{k} at vertex {r - 1}")
+    return ptr, verts[:n]

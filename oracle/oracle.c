@@ -18,6 +18,9 @@
  *   oracle_check       validity + the d+1 bound of Sec. 2.1
  *   oracle_chi         exact chromatic number by exhaustive search (n <= 12)
  *   oracle_csr_check   input well-formedness (symmetric, sorted, simple)
+ *   oracle_classes     colour classes: the vertices grouped by colour, each
+ *                      group in increasing id (the independent sets a
+ *                      colouring is computed for, Sec. 1)
  *
  * Colours are 1-based; 0 means "not coloured" (Sec. 2.1 numbers colours
  * 1..d+1 and Algorithm 1 forbids only the colours of *coloured* neighbours).
@@ -419,4 +422,29 @@ int32_t oracle_chi(int32_t n, const int32_t *row_ptr, const int32_t *col_idx)
         if (try_colour(n, adj, 0, k, c)) return k;
     }
     return n;
+}
+
+/*
+ * Colour classes (Sec. 1: a colouring partitions V into independent sets
+ * whose vertices can be processed concurrently).  A stable counting sort by
+ * colour: count every colour, turn the counts into start offsets, then walk
+ * the vertices in increasing id and append each one to its colour's group.
+ *   colors[v] in 1..k for every v (else returns 1 + the first bad vertex)
+ *   ptr[0..k+1]: the vertices of colour c are verts[ptr[c] .. ptr[c+1])
+ *   (ptr[0] = ptr[1] = 0: there is no colour 0)
+ * Returns 0 on success.
+ */
+int64_t oracle_classes(int32_t n, const int32_t *colors, int32_t k, int32_t *ptr, int32_t *verts)
+{
+    for (int32_t v = 0; v < n; ++v)
+        if (colors[v] < 1 || colors[v] > k) return (int64_t)v + 1;
+    for (int32_t c = 0; c <= k + 1; ++c) ptr[c] = 0;
+    for (int32_t v = 0; v < n; ++v) ptr[colors[v] + 1] += 1;   /* count colour c at ptr[c+1] */
+    for (int32_t c = 1; c <= k + 1; ++c) ptr[c] += ptr[c - 1];  /* now ptr[c] = vertices of colour < c */
+    int32_t *next = (int32_t *)malloc(((size_t)k + 2) * sizeof(int32_t));
+    if (!next) return -1;
+    for (int32_t c = 0; c <= k + 1; ++c) next[c] = ptr[c];
+    for (int32_t v = 0; v < n; ++v) verts[next[colors[v]]++] = v;
+    free(next);
+    return 0;
 }

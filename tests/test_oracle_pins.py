@@ -331,3 +331,36 @@ def test_tri2d_64_facts():
     c = O.ff(g)
     assert grundy_ok(g, c)
     assert c.max() == 4
+
+
+# ---- colour classes (the independent sets of a colouring, Sec. 1) --------
+
+def test_classes_small_by_hand():
+    # colours of 6 vertices: 2 1 2 3 1 2 -> class 1 = {1,4}, 2 = {0,2,5}, 3 = {3}
+    ptr, verts = O.classes(np.array([2, 1, 2, 3, 1, 2], np.int32))
+    assert list(ptr) == [0, 0, 2, 5, 6]
+    assert list(verts) == [1, 4, 0, 2, 5, 3]
+
+
+def test_classes_match_a_stable_sort_and_are_independent_sets():
+    for g in (I.kuhn3d(8), I.rmat(9), I.tri2d(20, 30, jitter=0.3, seed=2), I.from_edges(5, [])):
+        c = O.ff(g)
+        k = int(c.max()) if g.n else 0
+        ptr, verts = O.classes(c, k)
+        # a different definition: numpy's stable argsort by colour
+        assert np.array_equal(verts, np.argsort(c, kind="stable"))
+        assert np.array_equal(np.diff(ptr)[1:], np.bincount(c, minlength=k + 1)[1:])
+        for col in range(1, k + 1):
+            members = verts[ptr[col]:ptr[col + 1]]
+            assert np.all(c[members] == col) and np.all(np.diff(members) > 0)
+            inset = np.zeros(g.n, bool)
+            inset[members] = True
+            for v in members:  # no edge inside a class
+                assert not inset[g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]]].any()
+    # a wider colour range than used leaves empty classes; out of range fails
+    ptr, verts = O.classes(np.array([1, 1], np.int32), 4)
+    assert list(ptr) == [0, 0, 2, 2, 2, 2]
+    with pytest.raises(ValueError):
+        O.classes(np.array([1, 0], np.int32), 2)
+    with pytest.raises(ValueError):
+        O.classes(np.array([3], np.int32), 2)
