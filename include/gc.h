@@ -320,6 +320,27 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, int32_t
 int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
                 int32_t *colors_out, gc_tune_result *result);
 
+/* ---- colour classes --------------------------------------------------- */
+
+/*
+ * The colour classes of a colouring: its vertices grouped by colour, each
+ * group in increasing id (a stable counting sort).  Sec. 1: the vertices of
+ * one colour are an independent set, so a consumer processes them
+ * concurrently, class after class.
+ *   colors:         DEVICE int32[n], every value in 1..num_colors
+ *                   (GC_ERR_ARG otherwise; the outputs are then unspecified)
+ *   class_ptr:      DEVICE int32[num_colors + 2]: the vertices of colour c
+ *                   are class_vertices[class_ptr[c] .. class_ptr[c+1]);
+ *                   class_ptr[0] = class_ptr[1] = 0
+ *   class_vertices: DEVICE int32[n]
+ * num_colors <= GC_CLASSES_MAX_COLORS.  Scratch comes from the context
+ * (about num_colors * n / 64 bytes, at most 256 MB).
+ * Enqueued on `stream`, then waited for; returns the status.
+ */
+#define GC_CLASSES_MAX_COLORS (1 << 20)
+int gc_color_classes(gc_ctx *ctx, const int32_t *colors, int32_t n, int32_t num_colors, int32_t *class_ptr,
+                     int32_t *class_vertices, void *stream);
+
 /* ---- serving: continuous batching of colouring requests ------------------ */
 
 /*

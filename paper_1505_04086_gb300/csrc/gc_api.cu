@@ -350,7 +350,7 @@ void gc_ctx_destroy(gc_ctx *c)
     cudaSetDevice(c->device);
     if (c->ev_done) cudaEventSynchronize(c->ev_done);
     for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
-                   &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->pitems, &c->stage_rp,
+                   &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->pitems, &c->cls, &c->stage_rp,
                    &c->stage_ci,
                    &c->stage_col})
         b->release();

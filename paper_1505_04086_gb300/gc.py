@@ -32,6 +32,7 @@ GC_ERR_CHECK = -9
 GC_ERR_NOT_FOUND = -10
 GC_ERR_TOO_LARGE = -11
 GC_NOALLOC_MAX_N = 262144
+GC_CLASSES_MAX_COLORS = 1 << 20
 
 # mode bits
 GC_ALG_RSOC = 0
@@ -118,6 +119,7 @@ _SIGS = {
                                          ctypes.POINTER(gc_tune_result)]),
     "gc_autotune": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                    ctypes.c_int32, _P, ctypes.POINTER(gc_tune_result)]),
+    "gc_color_classes": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "gc_server_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_size_t, ctypes.c_int,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts)]),
     "gc_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
@@ -324,6 +326,14 @@ def gc_autotune(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colors_
                             _ptr(colors_out), ctypes.byref(r))
     return int(rc), {"best": opts_dict(r.best), "best_ms": float(r.best_ms),
                      "default_ms": float(r.default_ms), "evaluated": int(r.evaluated)}
+
+
+def gc_color_classes(ctx: int, colors, n: int, num_colors: int, class_ptr, class_vertices, stream=None) -> int:
+    """Group the vertices of a colouring by colour (device arrays); returns
+    the status.  class_ptr has num_colors + 2 entries, class_vertices n."""
+    return int(load().gc_color_classes(ctypes.c_void_p(ctx), _ptr(colors), int(n), int(num_colors),
+                                       _ptr(class_ptr), _ptr(class_vertices),
+                                       ctypes.c_void_p(_stream_handle(stream))))
 
 
 class Plan:
