@@ -61,6 +61,8 @@ def _load():
             lib.oracle_chi.argtypes = [i32, P, P]
             lib.oracle_csr_check.restype = i64
             lib.oracle_csr_check.argtypes = [i32, i64, P, P]
+            lib.oracle_rsoc_det_from.restype = ctypes.c_int
+            lib.oracle_rsoc_det_from.argtypes = [i32, P, P, ctypes.c_int, i64, P, i32, P, ctypes.POINTER(_Stats)]
             lib.oracle_classes.restype = i64
             lib.oracle_classes.argtypes = [i32, P, i32, P, P]
             _lib = lib
@@ -172,3 +174,27 @@ def classes(colors, k: int | None = None) -> tuple[np.ndarray, np.ndarray]:
     if r != 0:
         raise ValueError(f"colour out of 1..{k} at vertex {r - 1}")
     return ptr, verts[:n]
+
+
+def rsoc_det_from(g, colors, touched, tie: int = TIE_LOWER_KEEPS, max_iters: int | None = None,
+                  round_cap: int = 4096) -> Result:
+    """Incremental recolouring: Algorithm 3's while-loop (snapshot reads)
+    from the colouring `colors` with U = `touched` (see oracle.c)."""
+    rp, ci = _arrays(g)
+    c = np.array(colors, dtype=np.int32, copy=True)
+    if c.size != g.n:
+        raise ValueError("colors must have n entries")
+    cc = c if g.n else np.zeros(1, np.int32)
+    t = np.ascontiguousarray(touched, dtype=np.int32)
+    tt = t if t.size else np.zeros(1, np.int32)
+    rs = np.zeros(round_cap, np.int32)
+    st = _Stats()
+    st.round_sizes = rs.ctypes.data
+    st.round_sizes_cap = round_cap
+    mi = max_iters if max_iters is not None else g.n + 1
+    status = _load().oracle_rsoc_det_from(g.n, rp.ctypes.data, ci.ctypes.data, int(tie), int(mi), tt.ctypes.data,
+                                          int(t.size), cc.ctypes.data, ctypes.byref(st))
+    if status == 1:
+        raise ValueError("touched vertex out of range")
+    return Result(c, status, int(st.iterations), int(st.conflicts), int(st.model_bytes), int(st.colors),
+                  int(st.distinct_colors), rs[: min(int(st.iterations), round_cap)].copy())

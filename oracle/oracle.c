@@ -18,6 +18,9 @@
  *   oracle_check       validity + the d+1 bound of Sec. 2.1
  *   oracle_chi         exact chromatic number by exhaustive search (n <= 12)
  *   oracle_csr_check   input well-formedness (symmetric, sorted, simple)
+ *   oracle_rsoc_det_from  incremental recolouring: Algorithm 3's while-loop
+ *                      (snapshot reading) started from a given colouring
+ *                      and the vertices an edit touched
  *   oracle_classes     colour classes: the vertices grouped by colour, each
  *                      group in increasing id (the independent sets a
  *                      colouring is computed for, Sec. 1)
@@ -447,4 +450,85 @@ int64_t oracle_classes(int32_t n, const int32_t *colors, int32_t k, int32_t *ptr
     for (int32_t v = 0; v < n; ++v) verts[next[colors[v]]++] = v;
     free(next);
     return 0;
+}
+
+/*
+ * Incremental recolouring.  Sec. 1 motivates colouring with meshes that an
+ * adaptivity loop keeps changing; after a local edit only the touched part
+ * needs repair.  This is the while-loop of Algorithm 3 with snapshot reads
+ * (as oracle_rsoc_det) started from the colouring c (updated in place) and
+ * U = the touched vertices (each listed once; repeats are ignored) instead
+ * of round 0 and U = V.  A vertex of U is defective if it is uncoloured (0)
+ * or a neighbour on its tie side shares its colour.  The caller lists every
+ * uncoloured vertex and both endpoints of every inserted edge (a removed
+ * edge creates no conflict).  Every round reads an explicit worklist.
+ */
+int oracle_rsoc_det_from(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int tie, int64_t max_iters,
+                         const int32_t *touched, int32_t n_touched, int32_t *c, oracle_stats *st)
+{
+    if (n < 0 || n_touched < 0 || !c || (n_touched > 0 && !touched)) return ORACLE_ERR_ARG;
+    int32_t dmax = max_degree(n, row_ptr);
+    int32_t *snap = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *U = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *L = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    char *seen = (char *)calloc((size_t)n + 1, 1);
+    int64_t *mark = (int64_t *)malloc(((size_t)dmax + 2) * sizeof(int64_t));
+    if (!snap || !U || !L || !seen || !mark) {
+        free(snap); free(U); free(L); free(seen); free(mark);
+        return ORACLE_ERR_OOM;
+    }
+    for (int32_t k = 0; k < dmax + 2; ++k) mark[k] = -1;
+    int64_t nu = 0;
+    for (int32_t i = 0; i < n_touched; ++i) {
+        int32_t v = touched[i];
+        if (v < 0 || v >= n) {
+            free(snap); free(U); free(L); free(seen); free(mark);
+            return ORACLE_ERR_ARG;
+        }
+        if (!seen[v]) {
+            seen[v] = 1;
+            U[nu++] = v;
+        }
+    }
+    int64_t stamp = 0, bytes = 0, iters = 0, conflicts = 0;
+    int rc = ORACLE_OK;
+    while (nu > 0) {
+        if (iters >= max_iters) { rc = ORACLE_ERR_NO_CONVERGENCE; break; }
+        ++iters;
+        memcpy(snap, c, (size_t)n * sizeof(int32_t));
+        int64_t nl = 0;
+        for (int64_t i = 0; i < nu; ++i) {
+            int32_t v = U[i];
+            int defective = snap[v] == 0;
+            int64_t tie_side = 0;
+            for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                int32_t u = col_idx[k];
+                if (!loses_to(v, u, tie)) continue;
+                ++tie_side;
+                if (snap[u] == snap[v]) defective = 1;
+            }
+            int32_t deg = row_ptr[v + 1] - row_ptr[v];
+            bytes += 4 + 8 + 4;
+            if (defective) {
+                c[v] = first_fit(v, row_ptr, col_idx, snap, mark, stamp++);
+                L[nl++] = v;
+                bytes += 8 * (int64_t)deg + 4 + 4;
+            } else {
+                bytes += 8 * tie_side;
+            }
+        }
+        if (st && st->round_sizes && iters - 1 < st->round_sizes_cap)
+            st->round_sizes[iters - 1] = (int32_t)nl;
+        conflicts += nl;
+        int32_t *t = U; U = L; L = t;
+        nu = nl;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->conflicts = conflicts;
+        st->model_bytes = bytes;
+        colour_counts(n, c, st);
+    }
+    free(snap); free(U); free(L); free(seen); free(mark);
+    return rc;
 }

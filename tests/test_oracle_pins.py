@@ -364,3 +364,63 @@ def test_classes_match_a_stable_sort_and_are_independent_sets():
         O.classes(np.array([1, 0], np.int32), 2)
     with pytest.raises(ValueError):
         O.classes(np.array([3], np.int32), 2)
+
+
+# ---- incremental recolouring (Algorithm 3's loop from a given colouring) --
+
+def _add_edges(g, extra):
+    e = [(v, u) for v in range(g.n) for u in g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]] if u > v]
+    return I.from_edges(g.n, e + list(extra))
+
+
+def test_from_all_ones_and_all_touched_is_the_full_replay():
+    # Round 0 of the snapshot replay colours everything 1 and U^0 = V: starting
+    # the loop from that state must give the same run, bytes included (the
+    # 4 bytes a vertex of round 0 costs move to the first explicit worklist).
+    for g in (I.kuhn3d(6), I.rmat(8), I.tri2d(12, 9), I.from_edges(2, [(0, 1)])):
+        for tie in (O.TIE_LOWER_KEEPS, O.TIE_HIGHER_KEEPS):
+            full = O.rsoc_det(g, tie)
+            inc = O.rsoc_det_from(g, np.ones(g.n, np.int32), np.arange(g.n), tie)
+            assert np.array_equal(inc.colors, full.colors)
+            assert (inc.iterations, inc.conflicts, inc.model_bytes) == \
+                (full.iterations, full.conflicts, full.model_bytes)
+            assert np.array_equal(inc.round_sizes, full.round_sizes)
+
+
+def test_from_valid_colouring_changes_nothing():
+    g = I.kuhn3d(7)
+    c = O.ff(g)
+    none = O.rsoc_det_from(g, c, [])
+    assert none.iterations == 0 and np.array_equal(none.colors, c)
+    some = O.rsoc_det_from(g, c, [0, 5, 17, 5, 0])  # repeats are ignored
+    assert some.iterations == 1 and some.conflicts == 0 and np.array_equal(some.colors, c)
+    assert some.model_bytes == O.rsoc_det_from(g, c, [0, 5, 17]).model_bytes
+
+
+def test_from_repairs_an_edit_locally():
+    rng = np.random.default_rng(3)
+    g = I.tri2d(30, 30, jitter=0.3, seed=8)
+    c = O.ff(g)
+    # insert edges between equal-coloured vertices (conflicts by construction)
+    extra, touched = [], []
+    for _ in range(40):
+        v = int(rng.integers(g.n))
+        same = np.nonzero(c == c[v])[0]
+        u = int(same[rng.integers(same.size)])
+        if u != v:
+            extra.append((v, u))
+            touched += [v, u]
+    g2 = _add_edges(g, extra)
+    assert O.check(g2, c)[0] != 0
+    for tie in (O.TIE_LOWER_KEEPS, O.TIE_HIGHER_KEEPS):
+        r = O.rsoc_det_from(g2, c, touched, tie)
+        assert r.status == 0 and O.check(g2, r.colors)[0] == 0
+        changed = np.nonzero(r.colors != c)[0]
+        assert set(changed) <= set(touched)  # only touched vertices needed a new colour here
+    # uncoloured vertices listed as touched get coloured
+    c3 = c.copy()
+    c3[[3, 100, 400]] = 0
+    r = O.rsoc_det_from(g, c3, [3, 100, 400])
+    assert O.check(g, r.colors)[0] == 0 and np.all(r.colors[[3, 100, 400]] > 0)
+    with pytest.raises(ValueError):
+        O.rsoc_det_from(g, c, [g.n])
