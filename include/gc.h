@@ -223,6 +223,24 @@ int gc_color_async(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint3
                    const gc_opts *opts, int32_t *colors_out, void *stream);
 
 /*
+ * Incremental recolouring (no counterpart call in the paper; Sec. 1's
+ * adaptivity loops change a mesh locally): repair the colouring
+ * colors_inout (DEVICE, n entries, updated in place) of the graph csr
+ * after an edit, by Algorithm 3's while-loop started from those colours with
+ * the first worklist = touched (DEVICE int32[n_touched]; repeats are
+ * ignored; an id outside 0..n-1 gives GC_ERR_GRAPH) instead of round 0 and
+ * U = V.  A vertex inspected is defective if it is uncoloured (0) or a
+ * neighbour on its tie side shares its colour.  List every uncoloured
+ * vertex and both endpoints of every inserted edge; only listed vertices
+ * can change colour (with GC_FF_KEEPERS, also the higher neighbours a
+ * recoloured vertex clashes with).  GC_ALG_RSOC only (GC_SCHED_DET: bit-exact as the
+ * oracle's replay; GC_SCHED_ASYNC, GC_FF_KEEPERS allowed); no GC_TIERS or
+ * GC_REPAIR_SNAPSHOT.  Enqueued on `stream`; finish with gc_ctx_stats().
+ */
+int gc_recolor_async(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
+                     int32_t *colors_inout, const int32_t *touched, int32_t n_touched, void *stream);
+
+/*
  * Wait for the context's last enqueued colouring and report it.  Returns
  * that colouring's status (GC_OK, GC_ERR_NO_CONVERGENCE, GC_ERR_TIMEOUT,
  * GC_ERR_GRAPH, GC_ERR_CHECK, GC_ERR_OVERFLOW or GC_ERR_CUDA).  stats may
@@ -306,7 +324,10 @@ typedef struct {
  * vertex), tile, blocks_per_sm and tail (window, which changes which graphs
  * are coloured in id order and so the colour counts, stays automatic); each
  * candidate's cost is the median of `reps` (1..64) runs' device time
- * (CUDA events), and at most two sweeps are made.  Synchronous (legacy
+ * (CUDA events), and at most two sweeps are made.  In GC_SCHED_ASYNC the
+ * options change the colouring as well: a candidate is taken only if none of
+ * its runs used more colours than the default options' runs did (unless
+ * GC_NO_COLOR_STATS is set).  Synchronous (legacy
  * default stream); colors_out (device, total_n entries) receives the
  * colourings while it runs.  In GC_SCHED_DET mode every option set gives
  * the same colouring, so only speed is at stake.  Returns the first error

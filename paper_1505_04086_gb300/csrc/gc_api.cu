@@ -401,6 +401,46 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
     return rc;
 }
 
+int gc_recolor_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
+                     int32_t *colors_inout, const int32_t *touched, int32_t n_touched, void *stream)
+{
+    if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || n_touched < 0) return GC_ERR_ARG;
+    if (!gc::mode_ok(mode) || (mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_REPAIR_SNAPSHOT))) return GC_ERR_ARG;
+    if (n > 0 && (!csr->row_ptr || !colors_inout)) return GC_ERR_ARG;
+    if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
+    if (n_touched > 0 && !touched) return GC_ERR_ARG;
+    Resolved r;
+    int rc = resolve_opts(opts, n, r);
+    if (rc != GC_OK) return rc;
+    c->last.pending = false;
+    c->last.n = n;
+    c->last.mode = mode;
+    c->last.empty = (n == 0);
+    c->last.launch_status = GC_OK;
+    if (n == 0) {
+        c->last.pending = true;
+        return GC_OK;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return GC_ERR_CUDA;
+    if ((rc = ensure_scratch(c, n, gc::needs_second_buffer(mode), false, 0)) != GC_OK) return rc;
+    if ((rc = ensure_graph_tables(c, 1)) != GC_OK) return rc;
+    KParams p;
+    memset(&p, 0, sizeof p);
+    p.row_ptr = csr->row_ptr;
+    p.col_idx = csr->col_idx;
+    p.G = 1;
+    p.n = n;
+    p.nnz = nnz;
+    p.cA = colors_inout;
+    static const int32_t kNoTouched = 0;
+    p.touched = n_touched > 0 ? touched : &kNoTouched;  // non-null marks the incremental run
+    p.n_touched = n_touched;
+    rc = enqueue(c, p, false, mode, r, (cudaStream_t)stream);
+    if (rc == GC_OK) c->last.pending = true;
+    c->last.launch_status = rc;
+    return rc;
+}
+
 int gc_ctx_stats(gc_ctx *c, gc_stats *out)
 {
     if (!c) return GC_ERR_ARG;

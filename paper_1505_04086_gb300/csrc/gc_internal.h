@@ -29,11 +29,11 @@ constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entrie
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)
 constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
-constexpr int kLocalitySampleEntries = 32;  // locality: entries read per sampled vertex
+constexpr int kLocalitySampleEntries = 8;   // locality: entries read per sampled vertex
 constexpr int kOrderedGroup = 1 << 18;  // graphs this small without hubs or wide rows are ordered (round 0)
 constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order
 constexpr int kPipeMinChunks = 8;       // fewest chunks per warp of a group
-constexpr int kTargetSteps = 16;        // candidate chunk shares per grouped warp (x1.25 apart)
+constexpr int kTargetSteps = 32;        // candidate chunk shares per grouped warp (x1.1 apart)
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 
@@ -137,6 +137,8 @@ struct KParams {
     int64_t *uofs;             // G+1: prefix sums of the unordered graphs' chunk counts
     int32_t *olist;            // G: the ordered graphs
     int32_t *mark;             // GC_FF_KEEPERS: n entries, last iteration a vertex was queued in + 1
+    const int32_t *touched;    // incremental recolouring: the first worklist (null: normal colouring)
+    int32_t n_touched;
     int64_t *pitems;           // round 0: (graph, warp, group size) of each grouped warp
     int32_t pitems_cap;        // its capacity (>= the grid's warps)
 };

@@ -200,8 +200,12 @@ __device__ __forceinline__ void row_of(const KParams &p, int32_t v, int64_t &beg
         nbase = 0;
         g = 0;
     } else {
-        int gg = __ldg(p.gid_lut + (v >> kLutShift));
-        while (gg + 1 < p.G && __ldg(p.vtx_off + gg + 1) <= (int64_t)v) ++gg;
+        // lookup table per 2^kLutShift ids: -(g+1) if the whole block of ids
+        // lies in graph g, else g = the graph of its first id (step on)
+        const int e = __ldg(p.gid_lut + (v >> kLutShift));
+        int gg = e < 0 ? -e - 1 : e;
+        if (e >= 0)
+            while (gg + 1 < p.G && __ldg(p.vtx_off + gg + 1) <= (int64_t)v) ++gg;
         const int64_t vo = __ldg(p.vtx_off + gg);
         const int64_t eo = __ldg(p.edge_off + gg);
         const int32_t *rp = p.row_ptr + (p.rp_off ? __ldg(p.rp_off + gg) : vo + gg);
@@ -423,7 +427,7 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
     }
     const int cv = ld_color<ASYNC>(R + v);
     mb += 4;
-    const bool d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t);
+    const bool d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t) || cv == 0;
     if (op == OP_DETECT) {
         if (!ASYNC) st_color<false>(p.cA + v, cv);  // two-phase: bring buffer A up to date
         mb += 8ll * t + (d ? 4 : 0);
@@ -575,7 +579,7 @@ __device__ __noinline__ bool vertex_warp(const KParams &p, int op, int32_t v, in
         const int cv = ld_color<ASYNC>(R + v);
         add += 4;
         int t;
-        d = detect_warp<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, lane, t);
+        d = detect_warp<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, lane, t) || cv == 0;
         if (op == OP_DETECT) {
             if (!ASYNC && lane == 0) st_color<false>(p.cA + v, cv);
             add += 8ll * t + (d ? 4 : 0);
@@ -748,7 +752,7 @@ __device__ __noinline__ bool vertex_block(const KParams &p, int op, int32_t v, i
         const int cv = ld_color<ASYNC>(R + v);
         add += 4;
         int t;
-        d = detect_block<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, sh, t);
+        d = detect_block<ASYNC>(p, v, beg, end, nbase, R, cv, op == OP_RSOC, sh, t) || cv == 0;
         if (op == OP_DETECT) {
             if (!ASYNC && threadIdx.x == 0) st_color<false>(p.cA + v, cv);
             add += 8ll * t + (d ? 4 : 0);
@@ -1698,12 +1702,12 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
         T += block_sum(c, sh);
     }
     // The chunks per grouped warp, `target`: the smallest of kTargetSteps
-    // candidates (from the even share of all ordered chunks upwards, x1.25
+    // candidates (from the even share of all ordered chunks upwards, x1.1
     // each) at which the groups fit the budget and the graphs left to single
     // warps fit on the remaining warps at `target` chunks each.
     long long cand[kTargetSteps];
     cand[0] = max((T + warps - 1) / max(warps, 1ll), (long long)kPipeMinChunks);
-    for (int i = 1; i < kTargetSteps; ++i) cand[i] = cand[i - 1] + cand[i - 1] / 4 + 1;
+    for (int i = 1; i < kTargetSteps; ++i) cand[i] = cand[i - 1] + cand[i - 1] / 10 + 1;
     long long *acc = reinterpret_cast<long long *>(sh.hub_bm);  // [2 * kTargetSteps], block-local scratch
     for (int i = threadIdx.x; i < 2 * kTargetSteps; i += kBlock) acc[i] = 0;
     __syncthreads();
@@ -1821,6 +1825,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
     // Degree tiers (asynchronous RSOC): hubs, then mid-degree, then the rest.
     const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
     const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) != 0;
+    const bool recolor = p.touched != nullptr;  // incremental: start from the given colours
     unsigned nbl = gridDim.x;
     long long mb = 0;
     uint32_t phase = 0;  // parity bits of this warp's two staging barriers
@@ -1837,53 +1842,84 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // Deterministic round 0 colours every vertex from a snapshot in which
         // nothing is coloured yet, so every vertex gets colour 1.
         const long long stride = (long long)gridDim.x * kBlock;
-        for (long long b0 = (long long)blockIdx.x * kBlock; b0 < p.n; b0 += stride) {
-            const long long vi = b0 + threadIdx.x;
-            bool hub = false, midv = false;
-            const int32_t v = (int32_t)vi;
-            if (vi < p.n) {
-                int64_t beg, end;
-                int32_t nbase, g;
-                row_of<BATCH>(p, v, beg, end, nbase, g);
-                hub = (end - beg) > p.t2;
-                midv = tiers && !hub && (end - beg) > p.t1;
-                if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
-                if (ASYNC && !hub && (end - beg) > kT1Max && __ldcg(&p.gstat[g].wide) == 0u)
-                    atomicOr(&p.gstat[g].wide, 1u);
-                st_color<false>(p.cA + v, ASYNC ? 0 : 1);
-                if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
+        PT_BEGIN(t_pro);
+        if (recolor && (!ASYNC || keep)) {
+            // Incremental recolouring needs no binning (no round 0): only the
+            // second snapshot buffer or the keepers marks are initialised.
+            for (long long v = (long long)blockIdx.x * kBlock + threadIdx.x; v < p.n; v += stride) {
+                if (!ASYNC) st_color<false>(p.cB + v, __ldcg(p.cA + v));  // both snapshot buffers start equal
                 if (keep) p.mark[v] = 0;
-                if (!ASYNC) mb += 4;
             }
-            const unsigned m = __ballot_sync(FULL_MASK, hub);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int ob = 0;
-                if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
-                ob = __shfl_sync(FULL_MASK, ob, leader);
-                if (hub) {
-                    const int o = ob + __popc(m & ((1u << lane) - 1u));
-                    if (o < p.hub_cap) __stcg(p.hub_all + o, v);
-                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+        }
+        // Four vertices per thread per step, their row lookups issued together
+        // (each is a chain of dependent loads in a batch).
+        constexpr int kProU = 4;
+        PT_BEGIN(t_bin);
+        for (long long b0 = (long long)blockIdx.x * kBlock; b0 < (recolor ? 0ll : (long long)p.n);
+             b0 += kProU * stride) {
+            int64_t degs[kProU];
+            int32_t gs[kProU];
+#pragma unroll
+            for (int u = 0; u < kProU; ++u) {
+                const long long vi = b0 + u * stride + threadIdx.x;
+                degs[u] = -1;
+                gs[u] = 0;
+                if (vi < p.n) {
+                    int64_t beg, end;
+                    int32_t nbase;
+                    row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, gs[u]);
+                    degs[u] = end - beg;
                 }
             }
-            const unsigned mm = __ballot_sync(FULL_MASK, midv);
-            if (mm) {
-                const int leader = __ffs(mm) - 1;
-                int ob = 0;
-                if (lane == leader) ob = atomicAdd(&st->mid_all_count, __popc(mm));
-                ob = __shfl_sync(FULL_MASK, ob, leader);
-                if (midv) {
-                    const int o = ob + __popc(mm & ((1u << lane) - 1u));
-                    if (o < p.n) __stcg(p.mid_all + o, v);
-                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+#pragma unroll
+            for (int u = 0; u < kProU; ++u) {
+                const long long vi = b0 + u * stride + threadIdx.x;
+                bool hub = false, midv = false;
+                const int32_t v = (int32_t)vi;
+                if (vi < p.n) {
+                    const int64_t deg = degs[u];
+                    const int32_t g = gs[u];
+                    hub = deg > p.t2;
+                    midv = tiers && !hub && deg > p.t1;
+                    if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
+                    if (ASYNC && !hub && deg > kT1Max && __ldcg(&p.gstat[g].wide) == 0u)
+                        atomicOr(&p.gstat[g].wide, 1u);
+                    st_color<false>(p.cA + v, ASYNC ? 0 : 1);
+                    if (!ASYNC && twop) st_color<false>(p.cB + v, 1);
+                    if (!ASYNC) mb += 4;
+                    if (keep) p.mark[v] = 0;
+                }
+                const unsigned m = __ballot_sync(FULL_MASK, hub);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int ob = 0;
+                    if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (hub) {
+                        const int o = ob + __popc(m & ((1u << lane) - 1u));
+                        if (o < p.hub_cap) __stcg(p.hub_all + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    }
+                }
+                const unsigned mm = __ballot_sync(FULL_MASK, midv);
+                if (mm) {
+                    const int leader = __ffs(mm) - 1;
+                    int ob = 0;
+                    if (lane == leader) ob = atomicAdd(&st->mid_all_count, __popc(mm));
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (midv) {
+                        const int o = ob + __popc(mm & ((1u << lane) - 1u));
+                        if (o < p.n) __stcg(p.mid_all + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    }
                 }
             }
         }
+        PT_END(p.st, 15, t_bin);
         if (BATCH && p.g_rounds)
             for (long long g = (long long)blockIdx.x * kBlock + threadIdx.x; g < p.G; g += stride)
                 p.g_rounds[g] = (__ldg(p.vtx_off + g + 1) > __ldg(p.vtx_off + g)) ? 1 : 0;
-        if (ASYNC) {
+        if (ASYNC && !recolor) {
             // Flags of the ordered round-0 pass, and (automatic window) a
             // sample of how far lower neighbours sit in id from their vertex.
             const long long ntiles = ((long long)p.n + p.tile - 1) / p.tile;
@@ -1901,13 +1937,18 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                         int64_t beg, end;
                         int32_t nbase;
                         row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, g);
-                        // at most kLocalitySampleEntries lower neighbours per sampled vertex
-                        const int64_t stop = min(end, beg + kLocalitySampleEntries);
-                        for (int64_t k = beg; k < stop; ++k) {
-                            const int32_t u = nbase + __ldg(p.col_idx + k);
-                            if (u >= (int32_t)vi) break;
-                            ++all;
-                            near += ((int32_t)vi - u) < kNearIds;
+                        // the first kLocalitySampleEntries entries of the row, loaded
+                        // together; the lower neighbours among them (a prefix: rows are
+                        // sorted) are the sample
+                        int32_t u[kLocalitySampleEntries];
+#pragma unroll
+                        for (int q = 0; q < kLocalitySampleEntries; ++q)
+                            u[q] = beg + q < end ? nbase + __ldg(p.col_idx + beg + q) : INT32_MAX;
+#pragma unroll
+                        for (int q = 0; q < kLocalitySampleEntries; ++q) {
+                            const bool lower = u[q] < (int32_t)vi;
+                            all += lower;
+                            near += lower && ((int32_t)vi - u[q]) < kNearIds;
                         }
                     }
                     const int g0 = __shfl_sync(FULL_MASK, g, 0);
@@ -1927,7 +1968,39 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 }
             }
         }
+        PT_END(p.st, 14, t_pro);
+        if (recolor)  // repeat filter of the touched list
+            for (long long w = (long long)blockIdx.x * kBlock + threadIdx.x; w < (long long)p.n / 32 + 1; w += stride)
+                p.done[w] = 0;
         grid_sync(st, nbl);
+        if (recolor) {
+            // Incremental recolouring: the touched vertices (each once) form
+            // the worklist of the first iteration; there is no round 0.
+            for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < p.n_touched; i += stride) {
+                const int32_t v = __ldg(p.touched + i);
+                if (v < 0 || v >= p.n) {
+                    atomicOr(&st->error, GC_EW_GRAPH);
+                    continue;
+                }
+                const unsigned bit = 1u << (v & 31);
+                if (atomicOr((unsigned *)p.done + (v >> 5), bit) & bit) continue;
+                int64_t beg, end;
+                int32_t nbase, g;
+                row_of<BATCH>(p, v, beg, end, nbase, g);
+                const unsigned long long deg = (unsigned long long)(end - beg);
+                if (deg > (unsigned long long)p.t2) {
+                    atomicAdd(&st->wl_packed[0], deg);
+                    const int idx = atomicAdd(&st->hub_count[0], 1);
+                    if (idx < p.hub_cap) __stcg(p.hub[0] + idx, v);
+                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+                } else {
+                    const int o = (int)(atomicAdd(&st->wl_packed[0], (1ull << kWorkBits) + deg) >> kWorkBits);
+                    if (o < p.n) __stcg(p.wl[0] + o, v);
+                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+                }
+            }
+            grid_sync(st, nbl);
+        }
 
         bool alive = ld_volatile(&st->error) == 0;
         const int hub_all_n = ld_volatile(&st->hub_all_count);
@@ -1936,7 +2009,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // Tile window for the round-0 pass over the graphs that are not
         // coloured in id order by one warp (window > 1 only).
         const int window = p.window > 1 ? p.window : -1;
-        if (ASYNC && alive) {
+        if (ASYNC && alive && !recolor) {
             // Ids of a naturally numbered mesh are local: neighbours would be
             // coloured concurrently unless the graph goes strictly in id order.
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
@@ -1950,7 +2023,9 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // next starts (vertices of later stages are still uncoloured then).
         PassIn stages[3];
         int nstages = 1;
-        if (tiers) {
+        if (recolor) {
+            stages[0] = PassIn{false, p.wl[0], packed_count(st, 0), p.hub[0], ld_volatile(&st->hub_count[0]), p.t2};
+        } else if (tiers) {
             stages[0] = PassIn{false, nullptr, 0, p.hub_all, hub_all_n, 0};
             stages[1] = PassIn{false, p.mid_all, mid_all_n, nullptr, 0, 0};
             stages[2] = PassIn{true, nullptr, p.n, nullptr, 0, p.t1};
@@ -1973,7 +2048,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             // snapshot rounds it also lists the vertices that can be in
             // conflict afterwards, and the first repair round inspects only
             // those (every other vertex of U^0 = V is provably clean).
-            if (ASYNC && !twop) {
+            if (ASYNC && !twop && !recolor) {
                 const bool suspects = !snap;
                 PT_BEGIN(t_r0);
                 run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, window);
@@ -2203,7 +2278,8 @@ __global__ void build_lut_kernel(const int64_t *vtx_off, int32_t G, int32_t n, i
             const int mid = (lo + hi + 1) >> 1;
             if (vtx_off[mid] <= x) lo = mid; else hi = mid - 1;
         }
-        lut[c] = lo;
+        const int64_t block_end = x + (1ll << kLutShift) < (int64_t)n ? x + (1ll << kLutShift) : (int64_t)n;
+        lut[c] = (lo + 1 >= G || vtx_off[lo + 1] >= block_end) ? -lo - 1 : lo;  // negative: one graph only
     }
 }
 

@@ -49,12 +49,14 @@ int run_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o, int
 // Coordinate descent over the option knobs (see gc_autotune_batch in gc.h):
 // run(o) enqueues one colouring with options o on the legacy stream.
 template <class Run>
-int tune(gc_ctx *ctx, int reps, gc_tune_result *out, Run run)
+int tune(gc_ctx *ctx, int reps, uint32_t mode, gc_tune_result *out, Run run)
 {
     memset(out, 0, sizeof *out);
-    // Device time of one option set: median over reps runs.
-    auto measure = [&](const gc_opts &o, float &ms) -> int {
+    // Device time of one option set (median over reps runs) and the most
+    // colours any of the runs used.
+    auto measure = [&](const gc_opts &o, float &ms, int &colors) -> int {
         std::vector<float> t;
+        colors = 0;
         for (int r = 0; r < reps; ++r) {
             int rc = run(o);
             gc_stats st;
@@ -62,12 +64,17 @@ int tune(gc_ctx *ctx, int reps, gc_tune_result *out, Run run)
             if (rc == GC_OK) rc = gc_ctx_stats(ctx, &st);
             if (rc != GC_OK) return rc;
             t.push_back(st.elapsed_ms);
+            colors = std::max(colors, st.colors);
         }
         std::sort(t.begin(), t.end());
         ms = t[t.size() / 2];
         ++out->evaluated;
         return GC_OK;
     };
+    // In the asynchronous modes the options change the colouring too: a
+    // candidate is taken only if it uses no more colours than the defaults
+    // did (colour statistics off: time alone).
+    const bool guard = (mode & GC_SCHED_ASYNC) && !(mode & GC_NO_COLOR_STATS);
     // The knobs (only those that leave the method's result alone: window,
     // which decides which graphs are coloured in id order, changes colour
     // counts and is not tuned), each with its candidate values.
@@ -89,7 +96,8 @@ int tune(gc_ctx *ctx, int reps, gc_tune_result *out, Run run)
     best.tile = 64;
     best.tail = 2048;
     float best_ms = 0.f;
-    int rc = measure(best, best_ms);
+    int default_colors = 0;
+    int rc = measure(best, best_ms, default_colors);
     if (rc != GC_OK) return rc;
     out->default_ms = best_ms;
     // Coordinate descent from the defaults: two sweeps over the knobs, each
@@ -104,8 +112,9 @@ int tune(gc_ctx *ctx, int reps, gc_tune_result *out, Run run)
                 o.*(k.field) = v;
                 if (o.t1 > o.t2) continue;  // thread bin above the warp bin
                 float ms = 0.f;
-                if ((rc = measure(o, ms)) != GC_OK) return rc;
-                if (ms < best_ms) {
+                int colors = 0;
+                if ((rc = measure(o, ms, colors)) != GC_OK) return rc;
+                if (ms < best_ms && (!guard || colors <= default_colors)) {
                     best_ms = ms;
                     best = o;
                     moved = true;
@@ -212,7 +221,8 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t rep
     if (!ctx || !out || !batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
         reps > 64)
         return GC_ERR_ARG;
-    return tune(ctx, reps, out, [&](const gc_opts &o) { return run_batch(ctx, b, mode, &o, colors_out, nullptr); });
+    return tune(ctx, reps, mode, out,
+                [&](const gc_opts &o) { return run_batch(ctx, b, mode, &o, colors_out, nullptr); });
 }
 
 int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
@@ -221,7 +231,7 @@ int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t
     if (!ctx || !out || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || !gc::mode_ok(mode) ||
         (n > 0 && (!csr->row_ptr || !colors_out)) || (nnz > 0 && !csr->col_idx) || reps < 1 || reps > 64)
         return GC_ERR_ARG;
-    return tune(ctx, reps, out,
+    return tune(ctx, reps, mode, out,
                 [&](const gc_opts &o) { return gc_color_async(ctx, csr, n, nnz, mode, &o, colors_out, nullptr); });
 }
 

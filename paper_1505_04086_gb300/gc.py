@@ -108,6 +108,8 @@ _SIGS = {
     "gc_color_async": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
                                       ctypes.c_uint32, ctypes.POINTER(gc_opts), _P, _P]),
     "gc_ctx_stats": (ctypes.c_int, [_P, ctypes.POINTER(gc_stats)]),
+    "gc_recolor_async": (ctypes.c_int, [_P, ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
+                                        ctypes.c_uint32, ctypes.POINTER(gc_opts), _P, _P, ctypes.c_int32, _P]),
     "gc_color_batch": (ctypes.c_int, [_P, ctypes.POINTER(gc_batch), ctypes.c_uint32,
                                       ctypes.POINTER(gc_opts), _P, _P, _P, _P]),
     "gc_plan_create": (ctypes.c_int, [ctypes.POINTER(gc_batch), ctypes.c_int, ctypes.c_uint32,
@@ -273,6 +275,18 @@ def gc_color_async(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colo
     return int(load().gc_color_async(ctypes.c_void_p(ctx), ctypes.byref(csr), int(n), int(nnz),
                                      int(mode), ctypes.byref(o) if o is not None else None,
                                      _ptr(colors_out), ctypes.c_void_p(_stream_handle(stream))))
+
+
+def gc_recolor_async(ctx: int, row_ptr, col_idx, n: int, nnz: int, mode: int, colors_inout, touched,
+                     opts=None, stream=None) -> int:
+    """Enqueue an incremental recolouring (device arrays); returns the
+    launch status.  Finish with gc_ctx_stats."""
+    csr = gc_csr(_ptr(row_ptr), _ptr(col_idx) if nnz else 0)
+    o = _opts(opts)
+    nt = int(touched.numel() if hasattr(touched, "numel") else len(touched))
+    return int(load().gc_recolor_async(ctypes.c_void_p(ctx), ctypes.byref(csr), int(n), int(nnz), int(mode),
+                                       ctypes.byref(o) if o is not None else None, _ptr(colors_inout),
+                                       _ptr(touched) if nt else 0, nt, ctypes.c_void_p(_stream_handle(stream))))
 
 
 def gc_ctx_stats(ctx: int, round_cap: int = 0):
