@@ -28,7 +28,7 @@ constexpr int kWorkBits = 33;           // pushed-degree sum field of wl_packed 
 constexpr int kTailWorkPerVertex = 16;  // tail hand-off: at most tail*16 entries left
 constexpr int kNearIds = 2048;          // locality: "near" lower neighbour id distance
 constexpr int kOrderedSmall = 16384;    // graphs this small are coloured in id order (round 0)
-constexpr int kLocalitySample = 16;     // locality: every 16th vertex is sampled
+constexpr int kLocalitySample = 64;     // locality: every 64th vertex is sampled
 constexpr int kLocalitySampleEntries = 8;   // locality: entries read per sampled vertex
 constexpr int kOrderedGroup = 1 << 18;  // graphs this small without hubs or wide rows are ordered (round 0)
 constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order

@@ -233,6 +233,9 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
+#ifndef GC_SINGLES_PIPE
+#define GC_SINGLES_PIPE 0  // tuning experiment: single-warp ordered graphs through pipe_graph
+#endif
 #ifndef GC_PASS_INLINE
 #define GC_PASS_INLINE __forceinline__
 #endif
@@ -1493,7 +1496,10 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
             const long long v0 = BATCH ? __ldg(p.vtx_off + g) : 0;
             const long long v1 = BATCH ? __ldg(p.vtx_off + g + 1) : p.n;
             const bool skip_higher = !tiered && __ldcg(&p.gstat[g].hubs) == 0;
-            seq_graph<BATCH>(p, sh, g, v0, v1, W, mb, phase, lane, wid, in.dmax, skip_higher, it, push);
+            if (GC_SINGLES_PIPE && skip_higher && __ldcg(&p.gstat[g].wide) == 0)
+                pipe_graph<BATCH>(p, sh, g, v0, v1, 0, 1, W, mb, phase, lane, wid);
+            else
+                seq_graph<BATCH>(p, sh, g, v0, v1, W, mb, phase, lane, wid, in.dmax, skip_higher, it, push);
         }
     }
     // Phase B: chunks claimed tile by tile (the unordered graphs only, in the
@@ -1859,16 +1865,49 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
              b0 += kProU * stride) {
             int64_t degs[kProU];
             int32_t gs[kProU];
+            if (BATCH && !p.rp_off) {
+                // Graph g's row pointers start at row_ptr + vtx_off[g] + g, so
+                // vertex v's are row_ptr[v + g], row_ptr[v + g + 1]: only g is
+                // looked up, and the loads of the four vertices are issued
+                // stage by stage so that they overlap.
+                int e[kProU];
 #pragma unroll
-            for (int u = 0; u < kProU; ++u) {
-                const long long vi = b0 + u * stride + threadIdx.x;
-                degs[u] = -1;
-                gs[u] = 0;
-                if (vi < p.n) {
-                    int64_t beg, end;
-                    int32_t nbase;
-                    row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, gs[u]);
-                    degs[u] = end - beg;
+                for (int u = 0; u < kProU; ++u) {
+                    const long long vi = b0 + u * stride + threadIdx.x;
+                    e[u] = vi < p.n ? __ldg(p.gid_lut + (vi >> kLutShift)) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kProU; ++u) {
+                    const long long vi = b0 + u * stride + threadIdx.x;
+                    int gg = e[u] < 0 ? -e[u] - 1 : e[u];
+                    if (e[u] >= 0 && vi < p.n)  // the block of ids spans graphs (rare)
+                        while (gg + 1 < p.G && __ldg(p.vtx_off + gg + 1) <= vi) ++gg;
+                    gs[u] = gg;
+                }
+                int32_t r0[kProU], r1[kProU];
+#pragma unroll
+                for (int u = 0; u < kProU; ++u) {
+                    const long long vi = b0 + u * stride + threadIdx.x;
+                    r0[u] = r1[u] = 0;
+                    if (vi < p.n) {
+                        r0[u] = __ldg(p.row_ptr + vi + gs[u]);
+                        r1[u] = __ldg(p.row_ptr + vi + gs[u] + 1);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kProU; ++u) degs[u] = (int64_t)r1[u] - r0[u];
+            } else {
+#pragma unroll
+                for (int u = 0; u < kProU; ++u) {
+                    const long long vi = b0 + u * stride + threadIdx.x;
+                    degs[u] = -1;
+                    gs[u] = 0;
+                    if (vi < p.n) {
+                        int64_t beg, end;
+                        int32_t nbase;
+                        row_of<BATCH>(p, (int32_t)vi, beg, end, nbase, gs[u]);
+                        degs[u] = end - beg;
+                    }
                 }
             }
 #pragma unroll
