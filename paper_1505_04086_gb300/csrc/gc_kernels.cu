@@ -233,9 +233,6 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 #define GC_MIN_BLOCKS 3
 #endif
 constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
-#ifndef GC_SINGLES_PIPE
-#define GC_SINGLES_PIPE 0  // tuning experiment: single-warp ordered graphs through pipe_graph
-#endif
 #ifndef GC_PASS_INLINE
 #define GC_PASS_INLINE __forceinline__
 #endif
@@ -1496,10 +1493,7 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
             const long long v0 = BATCH ? __ldg(p.vtx_off + g) : 0;
             const long long v1 = BATCH ? __ldg(p.vtx_off + g + 1) : p.n;
             const bool skip_higher = !tiered && __ldcg(&p.gstat[g].hubs) == 0;
-            if (GC_SINGLES_PIPE && skip_higher && __ldcg(&p.gstat[g].wide) == 0)
-                pipe_graph<BATCH>(p, sh, g, v0, v1, 0, 1, W, mb, phase, lane, wid);
-            else
-                seq_graph<BATCH>(p, sh, g, v0, v1, W, mb, phase, lane, wid, in.dmax, skip_higher, it, push);
+            seq_graph<BATCH>(p, sh, g, v0, v1, W, mb, phase, lane, wid, in.dmax, skip_higher, it, push);
         }
     }
     // Phase B: chunks claimed tile by tile (the unordered graphs only, in the
