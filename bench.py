@@ -368,7 +368,7 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, ff_colors = cpu_baseline(g, budget_s=12.0)
 
-    launches_per_call = 2  # color_kernel, color_stats_kernel
+    launches_per_call = 1  # color_kernel (colour statistics at its end)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -577,7 +577,7 @@ def run_batch(args, ws, rank, local):
                          "traffic": recorded_traffic(f"batch{args.graphs}", mode_name),
                          "kernel": "gc::color_kernel<async,batch>",
                          "algorithmic_bytes_per_launch": int(np.mean(mbs)), "kernel_ms": round(float(np.mean(kms)), 4)},
-            "gpu_launches": 3 * steps, "clocks": clocks}  # lut, colour, stats
+            "gpu_launches": 2 * steps, "clocks": clocks}  # lut, colour
     plan.close()
     ctx.close()
     if ws > 1:

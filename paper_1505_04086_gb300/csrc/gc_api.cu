@@ -142,6 +142,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     if ((e = cudaMemsetAsync(c->gstat.p, 0, (size_t)std::max(p.G, 1) * sizeof(gc::GraphStat), s)) != cudaSuccess)
         return cuda_status(e);
     const bool stats = !(mode & GC_NO_COLOR_STATS);
+    p.stats_bitmap = stats ? c->bitmap.as<uint32_t>() : nullptr;  // computed at the end of the colouring kernel
     if (batch && (e = gc::launch_build_lut(p.vtx_off, p.G, p.n, c->lut.as<int32_t>(), s)) != cudaSuccess)
         return cuda_status(e);
     if ((mode & GC_VALIDATE) && (e = gc::launch_validate(p, batch, aux_grid, s)) != cudaSuccess)
@@ -151,8 +152,6 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     if ((e = gc::launch_color(p, async, batch, grid, s)) != cudaSuccess) return cuda_status(e);
     if ((e = record(c, c->ev1, s)) != cudaSuccess) return cuda_status(e);
     if ((mode & GC_CHECKED) && (e = gc::launch_check(p, batch, aux_grid, s)) != cudaSuccess)
-        return cuda_status(e);
-    if (stats && (e = gc::launch_color_stats(p.cA, p.n, p.st, c->bitmap.as<uint32_t>(), aux_grid, s)) != cudaSuccess)
         return cuda_status(e);
     if ((e = cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_status(e);

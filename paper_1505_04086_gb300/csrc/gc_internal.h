@@ -137,6 +137,7 @@ struct KParams {
     int64_t *uofs;             // G+1: prefix sums of the unordered graphs' chunk counts
     int32_t *olist;            // G: the ordered graphs
     int32_t *mark;             // GC_FF_KEEPERS: n entries, last iteration a vertex was queued in + 1
+    uint32_t *stats_bitmap;    // colour statistics at the end of the launch (null: none); zero on entry
     const int32_t *touched;    // incremental recolouring: the first worklist (null: normal colouring)
     int32_t n_touched;
     int64_t *pitems;           // round 0: (graph, warp, group size) of each grouped warp
@@ -158,8 +159,6 @@ cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cud
 cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm);
 size_t color_smem_bytes();
 cudaError_t prepare_color_kernels();  // opt in to the kernel's dynamic shared memory
-cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, uint32_t *bitmap,
-                               int grid, cudaStream_t s);
 cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s);
 cudaError_t launch_check(const KParams &p, bool batch, int grid, cudaStream_t s);
 cudaError_t launch_build_lut(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut,

@@ -1811,6 +1811,8 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
     }
 }
 
+__device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap);
+
 template <bool ASYNC, bool BATCH>
 __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 {
@@ -2173,6 +2175,14 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         }
     }
 
+    // Colour statistics of the result in the same launch: every block,
+    // those that left the rounds early included, meets at one more grid
+    // barrier and scans its share of the colours.
+    if (p.stats_bitmap) {
+        grid_sync(st, gridDim.x);
+        colour_stats(p.cA, p.n, st, p.stats_bitmap);
+    }
+
     // flush the byte-model counter
     for (int o = 16; o > 0; o >>= 1) mb += __shfl_down_sync(FULL_MASK, mb, o);
     if (lane == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
@@ -2182,10 +2192,10 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 // auxiliary kernels
 // ------------------------------------------------------------------------
 
-// Largest colour and presence bitmap of colours; the last block to finish
-// counts the distinct colours and clears the bitmap for the next call (it
-// must be zero on entry).
-__global__ void color_stats_kernel(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
+// Largest colour and presence bitmap of colours over the grid; the last
+// block to finish counts the distinct colours and clears the bitmap for the
+// next call (it must be zero on entry).
+__device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
 {
     __shared__ int acc;
     __shared__ bool last;
@@ -2369,13 +2379,6 @@ cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm)
 }
 
 size_t color_smem_bytes() { return sizeof(Shared); }
-
-cudaError_t launch_color_stats(const int32_t *colors, int32_t n, DevState *st, uint32_t *bitmap, int grid,
-                               cudaStream_t s)
-{
-    color_stats_kernel<<<grid, 256, 0, s>>>(colors, n, st, bitmap);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s)
 {

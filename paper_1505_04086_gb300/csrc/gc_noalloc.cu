@@ -192,6 +192,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     if (grid < 1) grid = 1;
     const int aux_grid = (int)(useful < (long long)d->num_sms * 8 ? (useful > 0 ? useful : 1) : d->num_sms * 8);
     const bool stats = !(mode & GC_NO_COLOR_STATS);
+    p.stats_bitmap = stats ? reinterpret_cast<uint32_t *>(base + kOffBitmap) : nullptr;
 
     // Clear what must start at zero: the launch state (the colour bitmap is
     // zero from load time and left zero by every statistics pass).
@@ -200,8 +201,6 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     if (e == cudaSuccess && (mode & GC_VALIDATE)) e = gc::launch_validate(p, false, aux_grid, st);
     if (e == cudaSuccess) e = gc::launch_color(p, async, false, (int)grid, st);
     if (e == cudaSuccess && (mode & GC_CHECKED)) e = gc::launch_check(p, false, aux_grid, st);
-    if (e == cudaSuccess && stats)
-        e = gc::launch_color_stats(p.cA, n, p.st, reinterpret_cast<uint32_t *>(base + kOffBitmap), aux_grid, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     gc::DevState h;
     if (e == cudaSuccess) e = cudaMemcpy(&h, p.st, sizeof h, cudaMemcpyDeviceToHost);

@@ -106,3 +106,24 @@ def test_autotune_single_graph():
     assert rc == gc.GC_OK
     assert np.array_equal(out.cpu().numpy(), O.rsoc_det(g).colors)
     ctx.close()
+
+
+@pytest.mark.parametrize("mode", [gc.GC_SCHED_ASYNC | gc.GC_FF_KEEPERS, gc.GC_SCHED_ASYNC | gc.GC_TIERS,
+                                  gc.GC_ALG_TWO_PHASE], ids=["keepers", "tiers", "twophase_det"])
+def test_plan_other_modes(mode):
+    b = small_batch()
+    vo, eo, rp, ci = dev_batch(b)
+    col = torch.zeros(b.total_n, dtype=torch.int32, device="cuda:0")
+    plan = gc.Plan(0, b.G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col)
+    for _ in range(2):
+        assert plan.launch() == gc.GC_OK
+        assert plan.stats()[0] == gc.GC_OK
+        c = col.cpu().numpy()
+        for g in range(b.G):
+            v0, v1 = int(b.vtx_off[g]), int(b.vtx_off[g + 1])
+            sub = b.graph(g)
+            if mode & gc.GC_SCHED_ASYNC:
+                assert O.check(sub, c[v0:v1])[0] == 0
+            else:
+                assert np.array_equal(c[v0:v1], O.twophase_det(sub).colors)
+    plan.close()

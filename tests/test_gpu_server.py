@@ -123,3 +123,18 @@ def test_destroy_with_requests_in_flight():
         assert rc == gc.GC_OK
     finally:
         srv2.close()
+
+
+@pytest.mark.parametrize("mode", [gc.GC_SCHED_ASYNC, gc.GC_SCHED_ASYNC | gc.GC_FF_KEEPERS,
+                                  gc.GC_SCHED_ASYNC | gc.GC_ALG_TWO_PHASE], ids=["async", "keepers", "twophase"])
+def test_async_modes_valid_per_request(mode):
+    gs = graphs(24, seed=5)
+    srv = gc.Server(0, budget_bytes=32 << 20, max_slots=32, mode=mode)
+    try:
+        tickets = [srv.submit(g.row_ptr, g.col_idx) for g in gs]
+        for g, t in zip(gs, tickets):
+            rc, col, st = srv.wait(t, g.n, timeout_ms=20000)
+            assert rc == gc.GC_OK
+            assert O.check(g, col)[0] == 0
+    finally:
+        srv.close()
