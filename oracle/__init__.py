@@ -63,6 +63,12 @@ def _load():
             lib.oracle_csr_check.argtypes = [i32, i64, P, P]
             lib.oracle_rsoc_det_from.restype = ctypes.c_int
             lib.oracle_rsoc_det_from.argtypes = [i32, P, P, ctypes.c_int, i64, P, i32, P, ctypes.POINTER(_Stats)]
+            lib.oracle_ff_d2.restype = i32
+            lib.oracle_ff_d2.argtypes = [i32, P, P, P]
+            lib.oracle_rsoc_det_d2.restype = ctypes.c_int
+            lib.oracle_rsoc_det_d2.argtypes = [i32, P, P, ctypes.c_int, i64, P, ctypes.POINTER(_Stats)]
+            lib.oracle_check_d2.restype = i64
+            lib.oracle_check_d2.argtypes = [i32, P, P, P]
             lib.oracle_classes.restype = i64
             lib.oracle_classes.argtypes = [i32, P, i32, P, P]
             _lib = lib
@@ -198,3 +204,27 @@ def rsoc_det_from(g, colors, touched, tie: int = TIE_LOWER_KEEPS, max_iters: int
         raise ValueError("touched vertex out of range")
     return Result(c, status, int(st.iterations), int(st.conflicts), int(st.model_bytes), int(st.colors),
                   int(st.distinct_colors), rs[: min(int(st.iterations), round_cap)].copy())
+
+
+def ff_d2(g) -> np.ndarray:
+    """Algorithm 1 over two-hop neighbourhoods (distance-2 colouring)."""
+    rp, ci = _arrays(g)
+    c = np.zeros(max(g.n, 1), np.int32)
+    if _load().oracle_ff_d2(g.n, rp.ctypes.data, ci.ctypes.data, c.ctypes.data) < 0:
+        raise MemoryError("oracle_ff_d2 failed")
+    return c[: g.n]
+
+
+def rsoc_det_d2(g, tie: int = TIE_LOWER_KEEPS, max_iters: int | None = None, round_cap: int = 4096) -> Result:
+    """Algorithm 3 (snapshot reads) over two-hop neighbourhoods."""
+    return _replay(_load().oracle_rsoc_det_d2, g, tie, max_iters, round_cap)
+
+
+def check_d2(g, colors) -> int:
+    """0 if no two vertices within two hops share a colour (and all are
+    coloured), else 1 + the first offending vertex."""
+    rp, ci = _arrays(g)
+    c = np.ascontiguousarray(colors, dtype=np.int32)
+    if c.size == 0:
+        c = np.zeros(1, np.int32)
+    return int(_load().oracle_check_d2(g.n, rp.ctypes.data, ci.ctypes.data, c.ctypes.data))

@@ -21,6 +21,10 @@
  *   oracle_rsoc_det_from  incremental recolouring: Algorithm 3's while-loop
  *                      (snapshot reading) started from a given colouring
  *                      and the vertices an edit touched
+ *   oracle_ff_d2, oracle_rsoc_det_d2
+ *                      distance-2 colouring (Sec. 6 names it as the variant
+ *                      that gains most): Algorithm 1 and the Algorithm 3
+ *                      replay with "neighbour" read as "within two hops"
  *   oracle_classes     colour classes: the vertices grouped by colour, each
  *                      group in increasing id (the independent sets a
  *                      colouring is computed for, Sec. 1)
@@ -531,4 +535,153 @@ int oracle_rsoc_det_from(int32_t n, const int32_t *row_ptr, const int32_t *col_i
     }
     free(snap); free(U); free(L); free(seen); free(mark);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Distance-2 colouring                                                 */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Distance-2 colouring asks two vertices joined by a path of one or two
+ * edges to differ in colour: the colouring of G^2, whose edges are those
+ * paths.  G^2 is not built: the two-hop neighbourhood D2(v) of v is read as
+ * "every u adjacent to v, and every w != v adjacent to such a u" (a vertex
+ * may be seen more than once; that changes nothing).
+ *
+ * Byte model of the distance-2 replay, per vertex inspected in a round:
+ *   4 for its worklist entry (every round after the first), 8 for its two
+ *   row pointers, 4 for its own colour, 16 per neighbour u (column index,
+ *   colour, and u's two row pointers), 8 per entry of u's row (column index
+ *   and colour), and 4 + 4 for the colour written and the push when it is
+ *   recoloured.  The conflict test and the First-Fit set come from one scan
+ *   of D2(v).  Round 0 colours every vertex 1: 4 bytes per vertex.
+ */
+
+/* Smallest colour >= 1 held by no coloured vertex of D2(v) in col, and
+ * whether a vertex of D2(v) on v's tie side holds colour cv (cv = 0: no
+ * test).  mark: scratch of at least d2max+2 entries. */
+static int32_t d2_scan(int32_t v, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *col, int tie,
+                       int32_t cv, int32_t d2max, int64_t *mark, int64_t stamp, int *conflict, int64_t *bytes)
+{
+    int c2 = 0;
+    int64_t b = 16 * (int64_t)(row_ptr[v + 1] - row_ptr[v]);
+    for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+        int32_t u = col_idx[k];
+        int32_t cu = col[u];
+        if (cu >= 1 && cu <= d2max + 1) mark[cu] = stamp;
+        if (cv && cu == cv && loses_to(v, u, tie)) c2 = 1;
+        b += 8 * (int64_t)(row_ptr[u + 1] - row_ptr[u]);
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            int32_t w = col_idx[j];
+            if (w == v) continue;
+            int32_t cw = col[w];
+            if (cw >= 1 && cw <= d2max + 1) mark[cw] = stamp;
+            if (cv && cw == cv && loses_to(v, w, tie)) c2 = 1;
+        }
+    }
+    int32_t k = 1;
+    while (mark[k] == stamp) ++k;
+    if (conflict) *conflict = c2;
+    if (bytes) *bytes += b;
+    return k;
+}
+
+/* An upper bound of |D2(v)| over v: sum of the neighbours' degrees. */
+static int32_t d2_bound(int32_t n, const int32_t *row_ptr, const int32_t *col_idx)
+{
+    int64_t best = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t s = 0;
+        for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) s += row_ptr[col_idx[k] + 1] - row_ptr[col_idx[k]];
+        if (s > best) best = s;
+    }
+    return best > INT32_MAX - 2 ? INT32_MAX - 2 : (int32_t)best;
+}
+
+/* Algorithm 1 over two-hop neighbourhoods, natural order. */
+int32_t oracle_ff_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *c)
+{
+    if (n < 0) return -1;
+    int32_t d2max = d2_bound(n, row_ptr, col_idx);
+    int64_t *mark = (int64_t *)malloc(((size_t)d2max + 2) * sizeof(int64_t));
+    if (!mark) return -1;
+    for (int32_t k = 0; k < d2max + 2; ++k) mark[k] = -1;
+    for (int32_t v = 0; v < n; ++v) c[v] = 0;
+    int32_t used = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        c[v] = d2_scan(v, row_ptr, col_idx, c, ORACLE_TIE_LOWER_KEEPS, 0, d2max, mark, v, NULL, NULL);
+        if (c[v] > used) used = c[v];
+    }
+    free(mark);
+    return used;
+}
+
+/* Algorithm 3 with snapshot reads over two-hop neighbourhoods (as
+ * oracle_rsoc_det, "neighbour" meaning "vertex of D2(v)"). */
+int oracle_rsoc_det_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int tie, int64_t max_iters,
+                       int32_t *c, oracle_stats *st)
+{
+    if (n < 0 || !c) return ORACLE_ERR_ARG;
+    int32_t d2max = d2_bound(n, row_ptr, col_idx);
+    int32_t *snap = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    int32_t *U = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *L = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int64_t *mark = (int64_t *)malloc(((size_t)d2max + 2) * sizeof(int64_t));
+    if (!snap || !U || !L || !mark) {
+        free(snap); free(U); free(L); free(mark);
+        return ORACLE_ERR_OOM;
+    }
+    for (int32_t k = 0; k < d2max + 2; ++k) mark[k] = -1;
+    int64_t stamp = 0, bytes = 4 * (int64_t)n, iters = 0, conflicts = 0;
+    for (int32_t v = 0; v < n; ++v) c[v] = 1;  /* round 0 over an uncoloured snapshot */
+    int64_t nu = n;
+    for (int32_t v = 0; v < n; ++v) U[v] = v;
+    int first_pass = 1, rc = ORACLE_OK;
+    while (nu > 0) {
+        if (iters >= max_iters) { rc = ORACLE_ERR_NO_CONVERGENCE; break; }
+        ++iters;
+        memcpy(snap, c, (size_t)n * sizeof(int32_t));
+        int64_t nl = 0;
+        for (int64_t i = 0; i < nu; ++i) {
+            int32_t v = U[i];
+            int defective = 0;
+            bytes += (first_pass ? 0 : 4) + 8 + 4;
+            int32_t k = d2_scan(v, row_ptr, col_idx, snap, tie, snap[v], d2max, mark, stamp++, &defective, &bytes);
+            if (defective) {
+                c[v] = k;
+                L[nl++] = v;
+                bytes += 4 + 4;
+            }
+        }
+        if (st && st->round_sizes && iters - 1 < st->round_sizes_cap)
+            st->round_sizes[iters - 1] = (int32_t)nl;
+        conflicts += nl;
+        int32_t *t = U; U = L; L = t;
+        nu = nl;
+        first_pass = 0;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->conflicts = conflicts;
+        st->model_bytes = bytes;
+        colour_counts(n, c, st);
+    }
+    free(snap); free(U); free(L); free(mark);
+    return rc;
+}
+
+/* Validity at distance 2: 0, or 1 + the first vertex sharing its colour
+ * with a vertex of D2(v) (or uncoloured). */
+int64_t oracle_check_d2(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int32_t *c)
+{
+    for (int32_t v = 0; v < n; ++v) {
+        if (c[v] < 1) return (int64_t)v + 1;
+        for (int32_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            int32_t u = col_idx[k];
+            if (c[u] == c[v]) return (int64_t)v + 1;
+            for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j)
+                if (col_idx[j] != v && c[col_idx[j]] == c[v]) return (int64_t)v + 1;
+        }
+    }
+    return 0;
 }

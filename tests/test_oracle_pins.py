@@ -424,3 +424,77 @@ def test_from_repairs_an_edit_locally():
     assert O.check(g, r.colors)[0] == 0 and np.all(r.colors[[3, 100, 400]] > 0)
     with pytest.raises(ValueError):
         O.rsoc_det_from(g, c, [g.n])
+
+
+# ---- distance-2 colouring (Sec. 6: colourings of G^d) -----------------------
+
+def square(g):
+    """G^2 built explicitly (edges = paths of one or two edges)."""
+    nbr = [set(g.col_idx[g.row_ptr[v]:g.row_ptr[v + 1]].tolist()) for v in range(g.n)]
+    e = set()
+    for v in range(g.n):
+        two = set(nbr[v])
+        for u in nbr[v]:
+            two |= nbr[u]
+        two.discard(v)
+        e |= {(min(v, w), max(v, w)) for w in two}
+    return I.from_edges(g.n, sorted(e))
+
+
+D2_GRAPHS = [lambda: I.from_edges(6, [(0, k) for k in range(1, 6)]),   # star: all distinct
+             lambda: I.from_edges(7, [(k, k + 1) for k in range(6)]),   # path: 3 colours
+             lambda: I.from_edges(5, [(k, (k + 1) % 5) for k in range(5)]),  # C5: its square is K5
+             lambda: I.kuhn3d(5), lambda: I.tri2d(9, 11, jitter=0.3, seed=2), lambda: I.rmat(7),
+             lambda: I.from_edges(4, [])]
+
+
+@pytest.mark.parametrize("make", D2_GRAPHS)
+def test_d2_first_fit_is_first_fit_of_the_square(make):
+    g = make()
+    c = O.ff_d2(g)
+    assert np.array_equal(c, O.ff(square(g)))
+    assert O.check_d2(g, c) == 0
+
+
+def test_d2_closed_forms():
+    star = I.from_edges(6, [(0, k) for k in range(1, 6)])
+    assert int(O.ff_d2(star).max()) == 6
+    path = I.from_edges(7, [(k, k + 1) for k in range(6)])
+    assert list(O.ff_d2(path)) == [1, 2, 3, 1, 2, 3, 1]
+    c5 = I.from_edges(5, [(k, (k + 1) % 5) for k in range(5)])
+    assert sorted(O.ff_d2(c5)) == [1, 2, 3, 4, 5]
+    c6 = I.from_edges(6, [(k, (k + 1) % 6) for k in range(6)])
+    assert int(O.ff_d2(c6).max()) == 3
+    # a planted error is caught: two vertices two hops apart share a colour
+    bad = O.ff_d2(path).copy()
+    bad[2] = bad[0]
+    assert O.check_d2(path, bad) != 0
+
+
+@pytest.mark.parametrize("make", D2_GRAPHS)
+@pytest.mark.parametrize("tie", [O.TIE_LOWER_KEEPS, O.TIE_HIGHER_KEEPS])
+def test_d2_replay_is_the_replay_of_the_square(make, tie):
+    # Same colours, iterations, conflicts and round sizes as the distance-1
+    # replay on G^2 (the byte models differ: G^2 is not built here).
+    g = make()
+    r2 = O.rsoc_det_d2(g, tie)
+    rs = O.rsoc_det(square(g), tie)
+    assert np.array_equal(r2.colors, rs.colors)
+    assert (r2.iterations, r2.conflicts) == (rs.iterations, rs.conflicts)
+    assert np.array_equal(r2.round_sizes, rs.round_sizes)
+    assert O.check_d2(g, r2.colors) == 0
+
+
+def test_d2_replay_bytes_by_hand():
+    # P3 (0-1-2), lower keeps, all colour 1 after round 0 (12 bytes).
+    # Iteration 1 over V (no worklist bytes); per vertex 8 + 4 + 16*deg +
+    # 8*(sum of the neighbours' degrees): v0 44, v1 60, v2 44; v1 and v2 see
+    # the lower vertex 0 with their colour and become 2 (+8 each): 164.
+    # Iteration 2 over {1, 2} (+4 each): v1 is clean (64); v2 now meets v1's
+    # 2 and becomes 3 (4 + 44 + 8 = 56): 120.  Iteration 3 over {2}: 48.
+    p3 = I.from_edges(3, [(0, 1), (1, 2)])
+    r = O.rsoc_det_d2(p3)
+    assert list(r.colors) == [1, 2, 3]
+    assert (r.iterations, r.conflicts) == (3, 3)
+    assert list(r.round_sizes) == [2, 1, 0]
+    assert r.model_bytes == 12 + 164 + 120 + 48
