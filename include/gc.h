@@ -21,8 +21,8 @@
  * graph gives an unspecified (but memory-safe for in-range indices)
  * colouring.
  *
- * Colours: int32, 1-based, in 1..deg(v)+1 on success; 0 is "uncoloured"
- * and never appears in a successful result.
+ * Colours: int32, 1-based, in 1..deg(v)+1 on success (1..|D2(v)|+1 with
+ * GC_DIST2); 0 is "uncoloured" and never appears in a successful result.
  *
  * Ownership: the caller owns every array it passes; the library never
  * frees or keeps them past the call (the server copies what it needs).
@@ -86,7 +86,7 @@ enum {
                                     through round 0 and its repair rounds before
                                     the next (later tiers are uncoloured while
                                     an earlier one is repaired) */
-    GC_FF_KEEPERS = 512          /* with GC_SCHED_ASYNC, GC_ALG_RSOC and
+    GC_FF_KEEPERS = 512,         /* with GC_SCHED_ASYNC, GC_ALG_RSOC and
                                     GC_TIE_LOWER_KEEPS only (else GC_ERR_ARG;
                                     not with GC_REPAIR_SNAPSHOT): a vertex's
                                     First-Fit choice, in round 0 and in every
@@ -101,10 +101,33 @@ enum {
                                     sequential First-Fit under heavy
                                     concurrency.  conflicts counts those
                                     handed-on neighbours too. */
+    GC_DIST2 = 1024              /* distance-2 colouring (Sec. 6 names it as the
+                                    next target of the method): two vertices
+                                    joined by a path of one or two edges get
+                                    different colours, i.e. the colouring of
+                                    G^2 without building it.  Algorithm 3 with
+                                    "neighbour" read as "vertex of D2(v)" (the
+                                    neighbours u of v and every w != v adjacent
+                                    to such a u).  Single graph only
+                                    (gc_color, gc_color_async; GC_ERR_ARG in
+                                    the batch, plan, server, no-alloc,
+                                    recolour and autotune calls) and only with
+                                    GC_ALG_RSOC, either schedule, either
+                                    tie-break, GC_VALIDATE, GC_CHECKED (checks
+                                    distance 2) and GC_NO_COLOR_STATS.
+                                    GC_SCHED_DET: round 0 gives every vertex
+                                    colour 1, then every round inspects U
+                                    against the colours of the end of the
+                                    round before (bit-exact replay).
+                                    GC_SCHED_ASYNC: round 0 is First-Fit over
+                                    D2(v) in place for every vertex, then
+                                    rounds over U = V, L, ... in place.
+                                    Colours lie in 1..|D2(v)|+1.  opts: only
+                                    max_rounds and blocks_per_sm apply. */
 };
 
 /* Every mode bit above. */
-#define GC_MODE_MASK 1023u
+#define GC_MODE_MASK 2047u
 
 /* ---- device error word bits (gc_stats.error_word) ---------------------- */
 enum {
@@ -137,7 +160,15 @@ typedef struct {
                                     (re)colouring, the tie side for a clean
                                     detection; 4 per colour written and per
                                     worklist push; 4 per vertex for a pass in
-                                    which nothing is coloured yet */
+                                    which nothing is coloured yet.  GC_DIST2:
+                                    per inspected vertex 4 (worklist entry,
+                                    not in a pass over all of V) + 8 + 4 (own
+                                    colour; not in the asynchronous round 0)
+                                    + 16 per neighbour u (index, colour, two
+                                    row pointers) + 8 per entry of u's row,
+                                    + 4 + 4 when recoloured (+ 4 for the
+                                    colour written in the asynchronous round
+                                    0); the deterministic round 0 moves 4n */
     float elapsed_ms;            /* device time of the colouring kernel(s) */
     int32_t *round_sizes;        /* optional caller-owned HOST array; receives
                                     |L| of each iteration */

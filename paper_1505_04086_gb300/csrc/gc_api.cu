@@ -83,9 +83,9 @@ int ensure_scratch(gc_ctx *c, int64_t n, bool need_b, bool batch, int64_t lut_en
     return GC_OK;
 }
 
-int grid_for(gc_ctx *c, bool async, bool batch, const Resolved &r, int64_t n)
+int grid_for(gc_ctx *c, bool async, bool batch, bool dist2, const Resolved &r, int64_t n)
 {
-    int occ = c->occ[async][batch];
+    int occ = dist2 ? c->occ_d2[async] : c->occ[async][batch];
     int bps = r.blocks_per_sm > 0 ? std::min(r.blocks_per_sm, occ) : occ;
     long long grid = (long long)bps * c->num_sms;
     // Never more blocks than there are vertices to share out.
@@ -147,12 +147,16 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
         return cuda_status(e);
     if ((mode & GC_VALIDATE) && (e = gc::launch_validate(p, batch, aux_grid, s)) != cudaSuccess)
         return cuda_status(e);
-    const int grid = grid_for(c, async, batch, r, n);
+    const bool dist2 = (mode & GC_DIST2) != 0;  // single graph only (checked by the callers)
+    const int grid = grid_for(c, async, batch, dist2, r, n);
     if ((e = record(c, c->ev0, s)) != cudaSuccess) return cuda_status(e);
-    if ((e = gc::launch_color(p, async, batch, grid, s)) != cudaSuccess) return cuda_status(e);
+    e = dist2 ? gc::launch_color_d2(p, async, grid, s) : gc::launch_color(p, async, batch, grid, s);
+    if (e != cudaSuccess) return cuda_status(e);
     if ((e = record(c, c->ev1, s)) != cudaSuccess) return cuda_status(e);
-    if ((mode & GC_CHECKED) && (e = gc::launch_check(p, batch, aux_grid, s)) != cudaSuccess)
-        return cuda_status(e);
+    if (mode & GC_CHECKED) {
+        e = dist2 ? gc::launch_check_d2(p, aux_grid, s) : gc::launch_check(p, batch, aux_grid, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
     if ((e = cudaMemcpyAsync(c->st_host, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_status(e);
     c->last.rounds_copied = gc::kStamps;  // DevState::round_head
@@ -206,7 +210,7 @@ int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, c
                      uint32_t mode, const gc_opts *opts, int32_t *colors_out, int32_t *rounds_out,
                      int64_t *conflicts_out, cudaStream_t s)
 {
-    if (!gc::mode_ok(mode)) return GC_ERR_ARG;
+    if (!gc::dist1_mode_ok(mode)) return GC_ERR_ARG;
     if (total_n > 0 && !colors_out) return GC_ERR_ARG;
     Resolved r;
     // The cap applies per graph; every graph's own bound is below total_n + 1.
@@ -310,6 +314,7 @@ int gc_ctx_create(gc_ctx **out, int device)
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     for (int a = 0; a < 2 && e == cudaSuccess; ++a)
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = gc::query_occupancy(a, b, &c->occ[a][b]);
+    for (int a = 0; a < 2 && e == cudaSuccess; ++a) e = gc::query_occupancy_d2(a, &c->occ_d2[a]);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_done, cudaEventDisableTiming);
@@ -323,9 +328,11 @@ int gc_ctx_create(gc_ctx **out, int device)
     // the colour-statistics kernel leaves the bitmap zero after every use
     if (rc == GC_OK && cudaMemset(c->bitmap.p, 0, gc::kStatBitmapWords * sizeof(uint32_t)) != cudaSuccess)
         rc = GC_ERR_CUDA;
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a) {
         for (int b = 0; b < 2; ++b)
             if (rc == GC_OK && c->occ[a][b] < 1) rc = GC_ERR_CUDA;
+        if (rc == GC_OK && c->occ_d2[a] < 1) rc = GC_ERR_CUDA;
+    }
     if (rc == GC_OK) {
         // one warp-group item per warp of the largest grid
         const int occ = std::max(std::max(c->occ[0][0], c->occ[0][1]), std::max(c->occ[1][0], c->occ[1][1]));
@@ -404,7 +411,7 @@ int gc_recolor_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint3
                      int32_t *colors_inout, const int32_t *touched, int32_t n_touched, void *stream)
 {
     if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || n_touched < 0) return GC_ERR_ARG;
-    if (!gc::mode_ok(mode) || (mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_REPAIR_SNAPSHOT))) return GC_ERR_ARG;
+    if (!gc::dist1_mode_ok(mode) || (mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_REPAIR_SNAPSHOT))) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_inout)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
     if (n_touched > 0 && !touched) return GC_ERR_ARG;

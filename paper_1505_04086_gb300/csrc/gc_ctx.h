@@ -66,7 +66,8 @@ int reserve_batch(gc_ctx *c, int32_t G, int64_t total_n, uint32_t mode);
 struct gc_ctx {
     int device = 0;
     int num_sms = 0;
-    int occ[2][2] = {{0, 0}, {0, 0}};
+    int occ[2][2] = {{0, 0}, {0, 0}};       // colouring kernel blocks per SM [async][batch]
+    int occ_d2[2] = {0, 0};                 // distance-2 kernel blocks per SM [async]
     // scratch
     gc::Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done, gstat, uofs, olist;
     gc::Buf pitems;                         // round-0 warp groups: one item per warp of the grid

@@ -1,0 +1,181 @@
+// Device primitives shared by the kernel translation units of libgc:
+// ordered loads and stores, colour accesses, the bounded grid barrier of
+// the persistent kernels and the colour statistics taken at their end.
+// Each .cu file compiles its own copy (no relocatable device code).
+#pragma once
+
+#include "gc_internal.h"
+
+namespace gc {
+
+#define FULL_MASK 0xffffffffu
+
+// Phase cycle accounting for tuning builds (-DGC_PHASE_TIMING): lane 0 of a
+// warp adds the clock64 cycles of a phase to DevState::dbg[slot].
+#ifdef GC_PHASE_TIMING
+#define PT_BEGIN(var) long long var = clock64()
+#define PT_END(st, slot, var)                                                          \
+    do {                                                                                \
+        if ((threadIdx.x & 31) == 0) atomicAdd(&(st)->dbg[slot], (unsigned long long)(clock64() - (var))); \
+    } while (0)
+#else
+#define PT_BEGIN(var)
+#define PT_END(st, slot, var)
+#endif
+
+constexpr unsigned long long kBarrierTimeoutNs = 10000000000ull;  // 10 s
+constexpr unsigned kBarrierMaxPolls = 1u << 28;
+
+// ------------------------------------------------------------------------
+// memory helpers
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_timer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+// Colour loads/stores.  Asynchronous mode reads colours that other threads
+// are writing in the same round: relaxed gpu-scope accesses, which are
+// coherent (never served from a stale L1 line).  Deterministic mode never
+// reads a buffer that is written in the same round; it still bypasses L1
+// (.cg) because the buffer was written in an earlier round of this launch.
+#ifndef GC_ASYNC_LOAD
+#define GC_ASYNC_LOAD 0
+#endif
+template <bool ASYNC>
+__device__ __forceinline__ int ld_color(const int32_t *p)
+{
+    if (ASYNC && GC_ASYNC_LOAD == 0) {
+        int v;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+        return v;
+    }
+    return __ldcg(p);
+}
+
+template <bool ASYNC>
+__device__ __forceinline__ void st_color(int32_t *p, int v)
+{
+    if (ASYNC)
+        asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    else
+        __stcg(p, v);
+}
+
+// ------------------------------------------------------------------------
+// grid barrier (bounded)
+// ------------------------------------------------------------------------
+
+// All nblocks blocks must be co-resident (cooperative launch).  A block that
+// waits longer than kBarrierTimeoutNs sets GC_EW_TIMEOUT and leaves; the
+// caller checks the error word after every barrier.
+static __device__ void grid_sync(DevState *st, unsigned nblocks)
+{
+    PT_BEGIN(t_bar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (nblocks > 1) {
+            unsigned gen = ld_acquire_u32(&st->bar_gen);
+            unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+            if (arrived == nblocks) {
+                atomicExch(&st->bar_count, 0u);
+                __threadfence();
+                st_release_u32(&st->bar_gen, gen + 1u);
+            } else {
+                unsigned long long t0 = global_timer();
+                unsigned polls = 0;
+                while (ld_acquire_u32(&st->bar_gen) == gen) {
+                    __nanosleep(64);
+                    if (++polls > kBarrierMaxPolls || global_timer() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(&st->error, GC_EW_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    PT_END(st, 8, t_bar);
+}
+
+// Whether a clash of v with u is v's to repair: u keeps its colour (lower
+// ids keep by default, higher ids with GC_TIE_HIGHER_KEEPS; no tie-break:
+// both repair).
+__device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
+{
+    return tie == TIE_LOWER ? u < v : (tie == TIE_HIGHER ? u > v : true);
+}
+
+// ------------------------------------------------------------------------
+// colour statistics
+// ------------------------------------------------------------------------
+
+// Largest colour and presence bitmap of colours over the grid; the last
+// block to finish counts the distinct colours and clears the bitmap for the
+// next call (it must be zero on entry).
+static __device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
+{
+    __shared__ int acc;
+    __shared__ bool last;
+    int mx = 0;
+    unsigned long long low = 0;  // colours 0..63, OR-reduced per warp
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = __ldcg(c + i);
+        mx = max(mx, x);
+        if (x >= 0 && x < 64) low |= 1ull << x;
+        else if (x >= 64 && x < kStatBitmapWords * 32) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_down_sync(FULL_MASK, mx, o));
+        low |= __shfl_down_sync(FULL_MASK, low, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx) atomicMax(&st->max_color, mx);
+        if (low & 0xffffffffull) atomicOr(&bitmap[0], (uint32_t)low);
+        if (low >> 32) atomicOr(&bitmap[1], (uint32_t)(low >> 32));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
+        acc = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int s = 0;
+    uint4 *bm4 = reinterpret_cast<uint4 *>(bitmap);
+    constexpr int kWords4 = kStatBitmapWords / 4;
+#pragma unroll 8
+    for (int w = threadIdx.x; w < kWords4; w += blockDim.x) {  // independent 16-byte loads in flight
+        uint4 x = __ldcg(bm4 + w);
+        if (x.x | x.y | x.z | x.w) bm4[w] = make_uint4(0u, 0u, 0u, 0u);
+        if (w == 0) x.x &= ~1u;  // colour 0 is not a colour
+        s += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w);
+    }
+    atomicAdd(&acc, s);
+    __syncthreads();
+    if (threadIdx.x == 0) st->distinct = acc;
+}
+
+}  // namespace gc

@@ -37,8 +37,9 @@ constexpr int kTargetSteps = 32;        // candidate chunk shares per grouped wa
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 
-// Mode bits a call accepts: GC_FF_KEEPERS only with asynchronous RSOC,
-// lower-keeps ties and in-place repairs.
+// Mode bits a single-graph colouring accepts: GC_FF_KEEPERS only with
+// asynchronous RSOC, lower-keeps ties and in-place repairs; GC_DIST2 only
+// with RSOC and neither of the repair variants.
 inline bool mode_ok(uint32_t mode)
 {
     if (mode & ~GC_MODE_MASK) return false;
@@ -46,8 +47,15 @@ inline bool mode_ok(uint32_t mode)
         (!(mode & GC_SCHED_ASYNC) ||
          (mode & (GC_ALG_TWO_PHASE | GC_TIE_HIGHER_KEEPS | GC_REPAIR_SNAPSHOT | GC_DEBUG_NO_TIEBREAK))))
         return false;
+    if ((mode & GC_DIST2) &&
+        (mode & (GC_ALG_TWO_PHASE | GC_DEBUG_NO_TIEBREAK | GC_REPAIR_SNAPSHOT | GC_TIERS | GC_FF_KEEPERS)))
+        return false;
     return true;
 }
+
+// Mode bits of the calls that colour with the distance-1 kernel only
+// (batches, plans, the server, the no-alloc and recolour calls, autotuning).
+inline bool dist1_mode_ok(uint32_t mode) { return mode_ok(mode) && !(mode & GC_DIST2); }
 
 // The second n-entry buffer holds colours (deterministic mode, snapshot
 // repairs) or, with GC_FF_KEEPERS, the round a vertex was last queued for.
@@ -161,6 +169,10 @@ size_t color_smem_bytes();
 cudaError_t prepare_color_kernels();  // opt in to the kernel's dynamic shared memory
 cudaError_t launch_validate(const KParams &p, bool batch, int grid, cudaStream_t s);
 cudaError_t launch_check(const KParams &p, bool batch, int grid, cudaStream_t s);
+// Distance-2 colouring (gc_d2.cu): the persistent kernel and the check.
+cudaError_t launch_color_d2(const KParams &p, bool async, int grid, cudaStream_t s);
+cudaError_t query_occupancy_d2(bool async, int *blocks_per_sm);
+cudaError_t launch_check_d2(const KParams &p, int grid, cudaStream_t s);
 cudaError_t launch_build_lut(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut,
                              cudaStream_t s);
 

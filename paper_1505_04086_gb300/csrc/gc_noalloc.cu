@@ -106,7 +106,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
                                 int32_t *colors_out, gc_stats *stats_out, void *stream)
 {
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
-    if (!gc::mode_ok(mode)) return GC_ERR_ARG;
+    if (!gc::dist1_mode_ok(mode)) return GC_ERR_ARG;
     if (n > kMaxN) return GC_ERR_TOO_LARGE;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;

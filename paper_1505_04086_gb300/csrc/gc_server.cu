@@ -386,7 +386,7 @@ extern "C" {
 
 int gc_server_create(gc_server **out, int device, size_t budget, int max_slots, uint32_t mode, const gc_opts *opts)
 {
-    if (!out || budget < 4096 || max_slots < 1 || !gc::mode_ok(mode)) return GC_ERR_ARG;
+    if (!out || budget < 4096 || max_slots < 1 || !gc::dist1_mode_ok(mode)) return GC_ERR_ARG;
     *out = nullptr;
     gc_server *s = new (std::nothrow) gc_server();
     if (!s) return GC_ERR_OOM;

@@ -137,7 +137,7 @@ int gc_plan_create(const gc_batch *b, int device, uint32_t mode, const gc_opts *
 {
     if (!out) return GC_ERR_ARG;
     *out = nullptr;
-    if (!batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out)) return GC_ERR_ARG;
+    if (!batch_ok(b) || !gc::dist1_mode_ok(mode) || (b->total_n > 0 && !colors_out)) return GC_ERR_ARG;
     int prev = 0;
     cudaGetDevice(&prev);
     gc_plan *pl = new (std::nothrow) gc_plan();
@@ -218,7 +218,7 @@ void gc_plan_destroy(gc_plan *pl)
 int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t reps, int32_t *colors_out,
                       gc_tune_result *out)
 {
-    if (!ctx || !out || !batch_ok(b) || !gc::mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
+    if (!ctx || !out || !batch_ok(b) || !gc::dist1_mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
         reps > 64)
         return GC_ERR_ARG;
     return tune(ctx, reps, mode, out,
@@ -228,7 +228,7 @@ int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t rep
 int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
                 int32_t *colors_out, gc_tune_result *out)
 {
-    if (!ctx || !out || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || !gc::mode_ok(mode) ||
+    if (!ctx || !out || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || !gc::dist1_mode_ok(mode) ||
         (n > 0 && (!csr->row_ptr || !colors_out)) || (nnz > 0 && !csr->col_idx) || reps < 1 || reps > 64)
         return GC_ERR_ARG;
     return tune(ctx, reps, mode, out,

@@ -48,6 +48,7 @@ GC_NO_COLOR_STATS = 64
 GC_REPAIR_SNAPSHOT = 128
 GC_TIERS = 256
 GC_FF_KEEPERS = 512
+GC_DIST2 = 1024
 
 # error word bits
 GC_EW_TIMEOUT = 1

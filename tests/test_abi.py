@@ -78,9 +78,10 @@ def test_mode_combinations_are_checked_on_the_host(lib):
     # argument valid, and the check comes before any device work.
     b = gc.gc_batch(0, 0, 0, 0, 0, 0, 0)
     h = ctypes.c_void_p()
-    K, A = gc.GC_FF_KEEPERS, gc.GC_SCHED_ASYNC
+    K, A, D2 = gc.GC_FF_KEEPERS, gc.GC_SCHED_ASYNC, gc.GC_DIST2
+    # distance-2 colouring is a single-graph mode: never a batch or plan
     for mode in (K, K | A | gc.GC_ALG_TWO_PHASE, K | A | gc.GC_TIE_HIGHER_KEEPS,
-                 K | A | gc.GC_REPAIR_SNAPSHOT, K | A | gc.GC_DEBUG_NO_TIEBREAK, 1 << 10, 1 << 31):
+                 K | A | gc.GC_REPAIR_SNAPSHOT, K | A | gc.GC_DEBUG_NO_TIEBREAK, D2, D2 | A, 1 << 11, 1 << 31):
         assert lib.gc_plan_create(ctypes.byref(b), 0, mode, None, None, None, None,
                                   ctypes.byref(h)) == gc.GC_ERR_ARG, mode
         assert not h.value
