@@ -491,6 +491,40 @@ void gc_server_destroy(gc_server *s);
 int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
                      int32_t *colors_out, gc_stats *stats_out, void *stream);
 
+/* ---- the paper's own form on the host cores ---------------------------- */
+
+/*
+ * Algorithms 2 and 3 as the paper runs them (Sec. 3, measured in Sec. 4):
+ * OpenMP threads over the CPU cores, every loop over U a parallel for with
+ * dynamic scheduling.  A separate host implementation for comparison beside
+ * the GPU calls: no GPU call ever runs it, and it touches no GPU.
+ *
+ *   csr, colors_out: HOST pointers (n+1, nnz and n int32 entries).
+ *   mode: GC_ALG_RSOC or GC_ALG_TWO_PHASE, GC_SCHED_ASYNC (colours read and
+ *         written in place by all threads, the paper's form; round 0 of RSOC
+ *         is First-Fit over V in place) or GC_SCHED_DET (every read of an
+ *         iteration sees the colours of the end of the iteration before:
+ *         the same colouring, iterations, conflicts and round sizes as
+ *         gc_color in GC_SCHED_DET, whatever the thread count), either
+ *         tie-break, GC_CHECKED (verify the result on the host;
+ *         GC_ERR_CHECK if invalid) and GC_NO_COLOR_STATS; any other bit gives
+ *         GC_ERR_ARG.
+ *   num_threads: OpenMP threads (0 = the OpenMP default).  With one thread
+ *         GC_SCHED_ASYNC RSOC is sequential First-Fit in id order.
+ *   stats_out (may be NULL): rounds, conflicts, colors, distinct_colors,
+ *         round_sizes (as for gc_ctx_stats), elapsed_ms = host wall time of
+ *         the colouring; model_bytes and error_word are 0.
+ * Returns GC_OK, GC_ERR_ARG, GC_ERR_OOM, GC_ERR_NO_CONVERGENCE (n+1
+ * iterations with conflicts left; colors_out holds the colouring at the cap)
+ * or GC_ERR_CHECK.  A malformed graph is not detected (keep indices in range).
+ */
+int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t num_threads,
+                  int32_t *colors_out, gc_stats *stats_out);
+
+/* Threads gc_host_color uses with num_threads = 0 (1 if the library was
+ * built without OpenMP). */
+int gc_host_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgc.so")
-SOURCES = ["gc_kernels.cu", "gc_api.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu", "gc_classes.cu", "gc_d2.cu"]
+SOURCES = ["gc_kernels.cu", "gc_api.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu", "gc_classes.cu", "gc_d2.cu",
+           "gc_host.cpp"]
 HEADERS = [os.path.join(CSRC, "gc_internal.h"), os.path.join(CSRC, "gc_device.cuh"), os.path.join(CSRC, "gc_ctx.h"),
            os.path.join(INCLUDE, "gc.h")]
 
@@ -36,6 +37,25 @@ def _cuda_lib_dir() -> str:
     if os.path.isabs(nv):
         return os.path.join(os.path.dirname(os.path.dirname(nv)), "lib64")
     return "/usr/local/cuda/lib64"
+
+
+_OPENMP = None
+
+
+def _openmp_flags() -> list:
+    """["-Xcompiler", "-fopenmp"] if the host compiler builds and links an
+    OpenMP program, else [] (gc_host_color then runs on one thread)."""
+    global _OPENMP
+    if _OPENMP is None:
+        import tempfile
+        with tempfile.TemporaryDirectory() as d:
+            src = os.path.join(d, "t.cpp")
+            with open(src, "w") as f:
+                f.write("#include <omp.h>\nint main() { return omp_get_max_threads() > 0 ? 0 : 1; }\n")
+            ok = subprocess.run(["g++", "-fopenmp", src, "-o", os.path.join(d, "t")],
+                                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL).returncode == 0
+        _OPENMP = ["-Xcompiler", "-fopenmp"] if ok else []
+    return _OPENMP
 
 
 def _stale(target: str, deps) -> bool:
@@ -61,10 +81,11 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(bdir, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            cmd = [nvcc] + common + ["-c", s, "-o", o + ".tmp"]
+            extra = _openmp_flags() if src.endswith(".cpp") else []
+            cmd = [nvcc] + common + extra + ["-c", s, "-o", o + ".tmp"]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((subprocess.Popen(cmd), o))
@@ -78,7 +99,7 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
         raise RuntimeError("nvcc failed while building libgc")
     if force or _stale(lib, objs):
         tmp = lib + f".tmp{os.getpid()}"
-        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
+        cmd = [nvcc] + ARCH + _openmp_flags() + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
             "-Xlinker", f"-rpath,{_cuda_lib_dir()}"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

@@ -50,41 +50,44 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t b
     bool hit = false;
     for (int64_t k0 = beg; k0 < end; k0 += 32) {
         const int64_t k = k0 + lane;
-        int64_t ub = 0, du = 0;
+        int ub = 0, du = 0;
         if (k < end) {
             const int32_t u = __ldg(p.col_idx + k);
             ub = __ldg(p.row_ptr + u);
-            du = (int64_t)__ldg(p.row_ptr + u + 1) - ub;
+            du = __ldg(p.row_ptr + u + 1) - ub;
             const int cu = ld_color<ASYNC>(R + u);
             d2_mark(bm, cu, base);
             if (test && cu == cv && on_tie_side(p.tie, u, v)) hit = true;
         }
         entries += du;
-        // the rows of this chunk's neighbours, laid end to end
-        long long incl = du;
+        // The rows of this chunk's neighbours laid end to end.  Distinct
+        // neighbours have disjoint rows, so the sum fits in 32 bits for any
+        // well-formed graph; a malformed one can only misplace entries, and
+        // the index check below keeps every load inside col_idx.
+        int incl = du;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(FULL_MASK, incl, o);
+            const int y = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += y;
         }
-        const long long total = __shfl_sync(FULL_MASK, incl, 31);
-        const long long excl = incl - du;
-        for (long long t0 = 0; t0 < total; t0 += 32 * kD2Unroll) {
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        const int excl = incl - du;
+        for (int t0 = 0; t0 < total; t0 += 32 * kD2Unroll) {
             int32_t w[kD2Unroll];
 #pragma unroll
             for (int j = 0; j < kD2Unroll; ++j) {
-                const long long t = t0 + j * 32 + lane;
-                const long long tc = t < total ? t : total - 1;
+                const int t = t0 + j * 32 + lane;
+                const int tc = t < total ? t : total - 1;
                 // owner lane: the number of lanes whose rows end at or before tc
                 int pos = 0;
 #pragma unroll
                 for (int s = 16; s > 0; s >>= 1) {
-                    const long long x = __shfl_sync(FULL_MASK, incl, pos + s - 1);
+                    const int x = __shfl_sync(FULL_MASK, incl, pos + s - 1);
                     if (x <= tc) pos += s;
                 }
-                const long long e0 = __shfl_sync(FULL_MASK, excl, pos);
-                const long long b0 = __shfl_sync(FULL_MASK, ub, pos);
-                w[j] = t < total ? __ldg(p.col_idx + b0 + (tc - e0)) : -1;
+                const unsigned idx = (unsigned)__shfl_sync(FULL_MASK, ub, pos) +
+                                     (unsigned)(tc - __shfl_sync(FULL_MASK, excl, pos));
+                w[j] = (t < total && idx < (unsigned long long)p.nnz) ? __ldg(p.col_idx + idx) : -1;
             }
 #pragma unroll
             for (int j = 0; j < kD2Unroll; ++j) {

@@ -1,0 +1,269 @@
+// The method in the paper's own form: OpenMP threads on the host cores
+// (Sec. 3; the paper measures it on multicore CPUs in Sec. 4).  Every loop
+// over the worklist U is a parallel for with dynamic scheduling; the end of
+// each loop is the barrier of Algorithms 2 and 3.
+//
+//   asynchronous RSOC (Algorithm 3): round 0 colours V by First-Fit in
+//     place, then every iteration inspects U in place: a vertex that shares
+//     its colour with a neighbour on its tie side is recoloured at once
+//     (First-Fit over all its neighbours' current colours) and joins L.
+//   asynchronous two-phase (Algorithm 2): every iteration recolours all of
+//     U in place (tentative phase), then, after the barrier, puts on L the
+//     vertices of U that share a colour with a neighbour on their tie side.
+//   deterministic forms: the same steps, each loop reading the colours of
+//     the end of the loop before (new colours are kept per worklist entry
+//     and written after the loop), so the result does not depend on the
+//     thread count or the schedule.
+//
+// Colours are read and written with relaxed atomics: in the asynchronous
+// forms threads race on them by design, as the paper's threads do.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "gc.h"
+
+namespace {
+
+constexpr uint32_t kHostModes = GC_ALG_TWO_PHASE | GC_SCHED_ASYNC | GC_TIE_HIGHER_KEEPS | GC_CHECKED | GC_NO_COLOR_STATS;
+
+inline int32_t ld(const int32_t *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
+inline void st(int32_t *p, int32_t v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
+
+struct Graph {
+    const int32_t *rp;
+    const int32_t *ci;
+    int32_t n;
+    bool higher_keeps;
+    // whether a clash of v with u is v's to repair
+    bool tie_side(int32_t u, int32_t v) const { return higher_keeps ? u > v : u < v; }
+};
+
+// Per-thread forbidden-colour marks: stamp[c] == cur means colour c is taken.
+struct Marks {
+    std::vector<int64_t> stamp;
+    int64_t cur = 0;
+};
+
+// Smallest colour >= 1 held by no neighbour of v in col.
+int32_t first_fit(const Graph &g, int32_t v, const int32_t *col, Marks &m)
+{
+    const int32_t deg = g.rp[v + 1] - g.rp[v];
+    ++m.cur;
+    for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) {
+        const int32_t c = ld(col + g.ci[k]);
+        if (c >= 1 && c <= deg + 1) m.stamp[c] = m.cur;
+    }
+    int32_t k = 1;
+    while (m.stamp[k] == m.cur) ++k;
+    return k;
+}
+
+// Whether a neighbour of v on its tie side holds colour cv in col.
+bool clashes(const Graph &g, int32_t v, int32_t cv, const int32_t *col)
+{
+    for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) {
+        const int32_t u = g.ci[k];
+        if (g.tie_side(u, v) && ld(col + u) == cv) return true;
+    }
+    return false;
+}
+
+int threads_for(int32_t req)
+{
+#ifdef _OPENMP
+    return req > 0 ? req : omp_get_max_threads();
+#else
+    (void)req;
+    return 1;
+#endif
+}
+
+int thread_id()
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+// Concatenate the threads' pushes into L (thread order).
+int64_t gather(std::vector<std::vector<int32_t>> &local, std::vector<int32_t> &L)
+{
+    size_t total = 0;
+    for (auto &x : local) total += x.size();
+    L.resize(total);
+    size_t o = 0;
+    for (auto &x : local) {
+        if (!x.empty()) memcpy(L.data() + o, x.data(), x.size() * sizeof(int32_t));
+        o += x.size();
+        x.clear();
+    }
+    return (int64_t)total;
+}
+
+struct Run {
+    int64_t iters = 0, conflicts = 0;
+    std::vector<int32_t> sizes;
+    bool capped = false;
+};
+
+void color_host(const Graph &g, uint32_t mode, int T, int32_t *c, int32_t max_deg, Run &r)
+{
+    const int32_t n = g.n;
+    const bool async = mode & GC_SCHED_ASYNC;
+    const bool twop = mode & GC_ALG_TWO_PHASE;
+    std::vector<Marks> marks(T);
+    for (auto &m : marks) m.stamp.assign((size_t)max_deg + 2, 0);
+    std::vector<std::vector<int32_t>> local(T);
+    std::vector<int32_t> U, L, fresh;  // fresh: deterministic forms, new colour per worklist entry
+    std::vector<char> flag;
+    bool all = true;                   // U = V (not materialised)
+    int64_t nu = n;
+
+    // RSOC round 0 (two-phase starts uncoloured: its first tentative phase
+    // is the same First-Fit over V)
+#pragma omp parallel for num_threads(T) schedule(static)
+    for (int32_t v = 0; v < n; ++v) st(c + v, (!twop && !async) ? 1 : 0);
+    if (!twop && async) {
+#pragma omp parallel for num_threads(T) schedule(dynamic, 256)
+        for (int32_t v = 0; v < n; ++v) st(c + v, first_fit(g, v, c, marks[thread_id()]));
+    }
+
+    const int64_t cap = (int64_t)n + 1;
+    while (nu > 0) {
+        if (r.iters >= cap) {
+            r.capped = true;
+            break;
+        }
+        ++r.iters;
+        if (!async) fresh.resize((size_t)nu);
+        if (twop) {
+            // tentative phase over U
+#pragma omp parallel for num_threads(T) schedule(dynamic, 256)
+            for (int64_t i = 0; i < nu; ++i) {
+                const int32_t v = all ? (int32_t)i : U[i];
+                const int32_t k = first_fit(g, v, c, marks[thread_id()]);
+                if (async) st(c + v, k);
+                else fresh[i] = k;
+            }
+            if (!async) {
+#pragma omp parallel for num_threads(T) schedule(static)
+                for (int64_t i = 0; i < nu; ++i) st(c + (all ? (int32_t)i : U[i]), fresh[i]);
+            }
+            // detection phase over U
+#pragma omp parallel for num_threads(T) schedule(dynamic, 256)
+            for (int64_t i = 0; i < nu; ++i) {
+                const int32_t v = all ? (int32_t)i : U[i];
+                if (clashes(g, v, ld(c + v), c)) local[thread_id()].push_back(v);
+            }
+        } else {
+            // fused detect-and-recolour over U
+            if (!async) flag.assign((size_t)nu, 0);
+#pragma omp parallel for num_threads(T) schedule(dynamic, 256)
+            for (int64_t i = 0; i < nu; ++i) {
+                const int32_t v = all ? (int32_t)i : U[i];
+                if (!clashes(g, v, ld(c + v), c)) continue;
+                const int32_t k = first_fit(g, v, c, marks[thread_id()]);
+                if (async) {
+                    st(c + v, k);
+                    local[thread_id()].push_back(v);
+                } else {
+                    fresh[i] = k;
+                    flag[i] = 1;
+                }
+            }
+            if (!async) {
+                for (int64_t i = 0; i < nu; ++i)
+                    if (flag[i]) {
+                        const int32_t v = all ? (int32_t)i : U[i];
+                        st(c + v, fresh[i]);
+                        local[0].push_back(v);
+                    }
+            }
+        }
+        const int64_t nl = gather(local, L);
+        r.sizes.push_back((int32_t)nl);
+        r.conflicts += nl;
+        U.swap(L);
+        nu = nl;
+        all = false;
+    }
+}
+
+}  // namespace
+
+extern "C" int gc_host_threads(void) { return threads_for(0); }
+
+extern "C" int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t num_threads,
+                             int32_t *colors_out, gc_stats *stats_out)
+{
+    if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX || num_threads < 0 || (mode & ~kHostModes)) return GC_ERR_ARG;
+    if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
+    if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
+    const Graph g{csr->row_ptr, csr->col_idx, n, (mode & GC_TIE_HIGHER_KEEPS) != 0};
+    int32_t max_deg = 0;
+    for (int32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, g.rp[v + 1] - g.rp[v]);
+    const int T = threads_for(num_threads);
+    Run r;
+    const auto t0 = std::chrono::steady_clock::now();
+    try {
+        if (n > 0) color_host(g, mode, T, colors_out, max_deg, r);
+    } catch (const std::bad_alloc &) {
+        return GC_ERR_OOM;
+    }
+    const auto t1 = std::chrono::steady_clock::now();
+    int status = r.capped ? GC_ERR_NO_CONVERGENCE : GC_OK;
+    if (status == GC_OK && (mode & GC_CHECKED)) {
+        for (int32_t v = 0; v < n && status == GC_OK; ++v) {
+            const int32_t cv = colors_out[v];
+            if (cv < 1 || cv > g.rp[v + 1] - g.rp[v] + 1) status = GC_ERR_CHECK;
+            for (int32_t k = g.rp[v]; k < g.rp[v + 1] && status == GC_OK; ++k)
+                if (colors_out[g.ci[k]] == cv) status = GC_ERR_CHECK;
+        }
+    }
+    if (stats_out) {
+        int32_t *rs = stats_out->round_sizes;
+        const int32_t rcap = stats_out->round_sizes_cap;
+        int64_t *rn = stats_out->round_ns;
+        const int32_t ncap = stats_out->round_ns_cap;
+        gc_stats s;
+        memset(&s, 0, sizeof s);
+        s.rounds = (int32_t)r.iters;
+        s.conflicts = r.conflicts;
+        s.colors = -1;
+        s.distinct_colors = -1;
+        if (!(mode & GC_NO_COLOR_STATS)) {
+            int32_t mx = 0;
+            for (int32_t v = 0; v < n; ++v) mx = std::max(mx, colors_out[v]);
+            std::vector<char> seen((size_t)mx + 1, 0);
+            int32_t d = 0;
+            for (int32_t v = 0; v < n; ++v)
+                if (colors_out[v] >= 1 && !seen[colors_out[v]]) {
+                    seen[colors_out[v]] = 1;
+                    ++d;
+                }
+            s.colors = mx;
+            s.distinct_colors = d;
+        }
+        s.elapsed_ms = std::chrono::duration<float, std::milli>(t1 - t0).count();
+        if (rs && rcap > 0)
+            for (int32_t i = 0; i < rcap && i < (int32_t)r.sizes.size(); ++i) rs[i] = r.sizes[i];
+        s.round_sizes = rs;
+        s.round_sizes_cap = rcap;
+        s.round_ns = rn;
+        s.round_ns_cap = ncap;
+        if (rn && ncap > 0) memset(rn, 0, (size_t)ncap * sizeof(int64_t));
+        *stats_out = s;
+    }
+    return status;
+}

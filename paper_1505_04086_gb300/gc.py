@@ -134,6 +134,9 @@ _SIGS = {
     "gc_color_noalloc": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts), _P,
                                         ctypes.POINTER(gc_stats), _P]),
+    "gc_host_color": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_int32, _P, ctypes.POINTER(gc_stats)]),
+    "gc_host_threads": (ctypes.c_int, []),
 }
 
 _lock = threading.Lock()
@@ -402,6 +405,26 @@ def gc_color_noalloc(row_ptr, col_idx, n: int, nnz: int, mode: int, colors_out, 
                                  ctypes.byref(o) if o is not None else None, _ptr(colors_out),
                                  ctypes.byref(st), ctypes.c_void_p(_stream_handle(stream)))
     return int(rc), stats_dict(st, rs, rn)
+
+
+def gc_host_color(row_ptr, col_idx, mode: int = 0, num_threads: int = 0, round_cap: int = 0):
+    """The paper's OpenMP form on the host cores (numpy int32 arrays, no
+    GPU).  Returns (status, colours, stats)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    n = rp.size - 1
+    col = np.zeros(max(n, 1), np.int32)
+    csr = gc_csr(rp.ctypes.data, ci.ctypes.data if ci.size else 0)
+    st = gc_stats()
+    rs, rn = _stats_buffers(st, round_cap)
+    rc = load().gc_host_color(ctypes.byref(csr), int(n), int(ci.size), int(mode), int(num_threads),
+                              col.ctypes.data, ctypes.byref(st))
+    return int(rc), col[:n], stats_dict(st, rs, rn)
+
+
+def gc_host_threads() -> int:
+    """OpenMP threads gc_host_color uses by default (1 without OpenMP)."""
+    return int(load().gc_host_threads())
 
 
 class Context:

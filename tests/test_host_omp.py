@@ -1,0 +1,78 @@
+"""The paper's own form on the host cores (gc_host_color, OpenMP).
+
+Its deterministic forms must equal the oracle's replays bit for bit at any
+thread count (colours, iterations, conflicts, round sizes); with one thread
+asynchronous RSOC is sequential First-Fit; with several threads the
+asynchronous forms must give proper colourings.  No GPU is involved.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1505_04086_gb300 import gc
+from paper_1505_04086_gb300 import inputs as I
+
+HIGHER = gc.GC_TIE_HIGHER_KEEPS
+TWOP = gc.GC_ALG_TWO_PHASE
+ASYNC = gc.GC_SCHED_ASYNC
+
+
+def graphs():
+    rng = np.random.default_rng(11)
+    out = [I.from_edges(1, []), I.from_edges(6, []), I.from_edges(2, [(0, 1)]),
+           I.from_edges(30, [(0, i) for i in range(1, 30)])]
+    for n in (17, 64):
+        out.append(I.from_edges(n, [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < 0.5]))
+    out += [I.kuhn3d(12), I.tri2d(30, 30, 0.2), I.rmat(10), I.rgg(3000)]
+    return out
+
+
+GRAPHS = graphs()
+IDS = [f"{g.name}-{g.n}" for g in GRAPHS]
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=IDS)
+@pytest.mark.parametrize("alg", [0, TWOP], ids=["rsoc", "twophase"])
+@pytest.mark.parametrize("tie", [0, HIGHER], ids=["lower", "higher"])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_host_det_matches_the_oracle_replay(g, alg, tie, threads):
+    rc, col, st = gc.gc_host_color(g.row_ptr, g.col_idx, alg | tie | gc.GC_CHECKED, threads, round_cap=4096)
+    otie = O.TIE_HIGHER_KEEPS if tie else O.TIE_LOWER_KEEPS
+    ref = (O.twophase_det if alg else O.rsoc_det)(g, otie)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    assert np.array_equal(col, ref.colors)
+    assert (st["rounds"], st["conflicts"]) == (ref.iterations, ref.conflicts)
+    assert np.array_equal(st["round_sizes"], ref.round_sizes)
+    if g.n:
+        assert (st["colors"], st["distinct_colors"]) == (ref.num_colors, ref.distinct_colors)
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=IDS)
+def test_host_async_rsoc_on_one_thread_is_sequential_first_fit(g):
+    rc, col, st = gc.gc_host_color(g.row_ptr, g.col_idx, ASYNC, 1)
+    assert rc == gc.GC_OK
+    assert np.array_equal(col, O.ff(g))
+    assert st["rounds"] == (1 if g.n else 0) and st["conflicts"] == 0
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=IDS)
+@pytest.mark.parametrize("alg", [0, TWOP], ids=["rsoc", "twophase"])
+@pytest.mark.parametrize("tie", [0, HIGHER], ids=["lower", "higher"])
+def test_host_async_is_a_proper_colouring(g, alg, tie):
+    rc, col, st = gc.gc_host_color(g.row_ptr, g.col_idx, alg | ASYNC | tie | gc.GC_CHECKED, 8)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    bad, mx, dist = O.check(g, col)
+    assert bad == 0
+    if g.n:
+        assert (st["colors"], st["distinct_colors"]) == (mx, dist)
+
+
+def test_host_mode_bits_are_checked():
+    g = I.kuhn3d(3)
+    for bad in (gc.GC_VALIDATE, gc.GC_DEBUG_NO_TIEBREAK, gc.GC_REPAIR_SNAPSHOT, gc.GC_TIERS, gc.GC_FF_KEEPERS,
+                gc.GC_DIST2, 1 << 20):
+        rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, ASYNC | bad, 2)
+        assert rc == gc.GC_ERR_ARG, bad
+    rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, 0, -1)
+    assert rc == gc.GC_ERR_ARG
+    assert gc.gc_host_threads() >= 1
