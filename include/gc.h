@@ -123,7 +123,8 @@ enum {
                                     D2(v) in place for every vertex, then
                                     rounds over U = V, L, ... in place.
                                     Colours lie in 1..|D2(v)|+1.  opts: only
-                                    max_rounds and blocks_per_sm apply. */
+                                    max_rounds, blocks_per_sm and d2_heavy
+                                    apply. */
 };
 
 /* Every mode bit above. */
@@ -208,6 +209,11 @@ typedef struct {
                                     without such vertices.  1 = every graph;
                                     -1 = none (pure speculation); k > 1 = none,
                                     and at most k tiles in flight */
+    int32_t d2_heavy;            /* GC_DIST2: a vertex whose two-hop
+                                    neighbourhood has more entries (sum of its
+                                    neighbours' degrees) than this is inspected
+                                    by a whole block, the others by one warp;
+                                    0 = 4096 */
 } gc_opts;
 
 typedef struct gc_ctx gc_ctx;

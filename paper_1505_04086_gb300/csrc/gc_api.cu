@@ -40,7 +40,7 @@ bool is_device_ptr(const void *p)
 }
 
 struct Resolved {
-    int32_t max_rounds, t1, t2, tile, tail, blocks_per_sm, window;
+    int32_t max_rounds, t1, t2, tile, tail, blocks_per_sm, window, d2_heavy;
 };
 
 int resolve_opts(const gc_opts *o, int64_t n, Resolved &r)
@@ -56,6 +56,8 @@ int resolve_opts(const gc_opts *o, int64_t n, Resolved &r)
     r.blocks_per_sm = o->blocks_per_sm;
     r.window = o->window;
     if (r.window < -1) return GC_ERR_ARG;
+    if (o->d2_heavy < 0) return GC_ERR_ARG;
+    r.d2_heavy = o->d2_heavy > 0 ? o->d2_heavy : 4096;
     if (r.t1 > gc::kT1Max || r.t2 > gc::kT2Max || r.t1 > r.t2) return GC_ERR_ARG;
     if (r.tile % 32 != 0 || r.tile > 4096) return GC_ERR_ARG;
     if (r.blocks_per_sm < 0) return GC_ERR_ARG;
@@ -122,6 +124,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.tile = r.tile;
     p.tail = r.tail;
     p.window = r.window;
+    p.d2_heavy = r.d2_heavy;
     p.done = c->done.as<int32_t>();
     p.gstat = c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();

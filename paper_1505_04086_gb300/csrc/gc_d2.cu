@@ -23,32 +23,52 @@
 // iteration i-1, so both buffers agree on it).  GC_SCHED_ASYNC: round 0 is
 // First-Fit over D2(v) for every vertex in place, then iterations over V,
 // L, ... read and write one buffer in place.
+#include <climits>
+
 #include "gc_device.cuh"
 
 namespace gc {
 namespace {
 
-constexpr int kD2Window = 2048;           // colours per First-Fit window
-constexpr int kD2Words = kD2Window / 32;  // window words per warp (2 per lane)
-constexpr int kD2Unroll = 4;              // batches of 32 two-hop entries in flight
+#ifndef GC_D2_UNROLL
+#define GC_D2_UNROLL 8
+#endif
+#ifndef GC_D2_MIN_BLOCKS
+#define GC_D2_MIN_BLOCKS 4
+#endif
+constexpr int kD2Window = 2048;             // colours per First-Fit window of a warp
+constexpr int kD2Words = kD2Window / 32;    // window words per warp (2 per lane)
+constexpr int kD2Unroll = GC_D2_UNROLL;     // batches of 32 two-hop entries in flight
+constexpr int kHeavyWindow = 32768;         // colours per First-Fit window of a block
+constexpr int kHeavyWords = kHeavyWindow / 32;
 
-// Mark colour c in the window of colours [base, base + kD2Window).
-__device__ __forceinline__ void d2_mark(uint32_t *bm, int c, int base)
+struct D2Shared {
+    uint32_t warp_bm[kWarps][kD2Words];
+    uint32_t block_bm[kHeavyWords];
+    int first_free;
+    int item;
+};
+
+// Mark colour c in the window of colours [base, base + window).
+__device__ __forceinline__ void d2_mark(uint32_t *bm, int c, int base, int window)
 {
     const unsigned o = (unsigned)(c - base);
-    if (o < (unsigned)kD2Window) atomicOr(bm + (o >> 5), 1u << (o & 31));
+    if (o < (unsigned)window) atomicOr(bm + (o >> 5), 1u << (o & 31));
 }
 
-// One read of D2(v) in the colour buffer R: mark every colour in the
-// window; return (per lane) whether a vertex of D2(v) on v's tie side holds
-// colour cv (only if test).  entries: the lane's share of the two-hop
-// entries read (the byte model's 8 per entry of a neighbour's row).
+// One read of this warp's share of D2(v) in the colour buffer R: the
+// neighbours at entries kfirst, kfirst + kstride, ... (chunks of 32) of v's
+// row, which ends at `end`, and their rows.  Marks every colour in the
+// window [base, base + window); returns (per lane) whether a vertex read on
+// v's tie side holds colour cv (only if test).  entries: the lane's share of
+// the two-hop entries read (the byte model's 8 per entry of a neighbour's
+// row).
 template <bool ASYNC>
-__device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t beg, int64_t end, int cv, bool test,
-                        int base, uint32_t *bm, int lane, long long &entries)
+__device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t kfirst, int64_t end, int kstride,
+                        int cv, bool test, int base, int window, uint32_t *bm, int lane, long long &entries)
 {
     bool hit = false;
-    for (int64_t k0 = beg; k0 < end; k0 += 32) {
+    for (int64_t k0 = kfirst; k0 < end; k0 += kstride) {
         const int64_t k = k0 + lane;
         int ub = 0, du = 0;
         if (k < end) {
@@ -56,7 +76,7 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t b
             ub = __ldg(p.row_ptr + u);
             du = __ldg(p.row_ptr + u + 1) - ub;
             const int cu = ld_color<ASYNC>(R + u);
-            d2_mark(bm, cu, base);
+            d2_mark(bm, cu, base, window);
             if (test && cu == cv && on_tie_side(p.tie, u, v)) hit = true;
         }
         entries += du;
@@ -93,7 +113,7 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t b
             for (int j = 0; j < kD2Unroll; ++j) {
                 if (w[j] >= 0 && w[j] != v) {
                     const int cw = ld_color<ASYNC>(R + w[j]);
-                    d2_mark(bm, cw, base);
+                    d2_mark(bm, cw, base, window);
                     if (test && cw == cv && on_tie_side(p.tie, w[j], v)) hit = true;
                 }
             }
@@ -102,11 +122,11 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t b
     return hit;
 }
 
-// Inspect v (warp-uniform) against R.  test: v holds colour cv and is
-// defective if a vertex of D2(v) on its tie side holds cv too; a clean v
-// returns cv.  Otherwise (and always without test) returns the smallest
-// colour >= 1 held by no vertex of D2(v).  mb: per-lane byte model, 8 per
-// two-hop entry of the first read.
+// Inspect v (warp-uniform) against R with one warp.  test: v holds colour
+// cv and is defective if a vertex of D2(v) on its tie side holds cv too; a
+// clean v returns cv.  Otherwise (and always without test) returns the
+// smallest colour >= 1 held by no vertex of D2(v).  mb: per-lane byte
+// model, 8 per two-hop entry of the first read.
 template <bool ASYNC>
 __device__ int d2_vertex(const KParams &p, const int32_t *R, int32_t v, int64_t beg, int64_t end, int cv, bool test,
                          uint32_t *bm, int lane, bool &defective, long long &mb)
@@ -119,7 +139,7 @@ __device__ int d2_vertex(const KParams &p, const int32_t *R, int32_t v, int64_t 
         __syncwarp();
         const bool first = base == 1;
         long long e = 0;
-        const bool hit = d2_read<ASYNC>(p, R, v, beg, end, cv, test && first, base, bm, lane, e);
+        const bool hit = d2_read<ASYNC>(p, R, v, beg, end, 32, cv, test && first, base, kD2Window, bm, lane, e);
         if (first) {
             mb += 8 * e;
             defective = __any_sync(FULL_MASK, hit);
@@ -142,29 +162,80 @@ __device__ int d2_vertex(const KParams &p, const int32_t *R, int32_t v, int64_t 
     }
 }
 
+// The same inspection of a heavy vertex by the whole block (block-uniform
+// v): warp w reads neighbour chunks w, w + kWarps, ... into one
+// kHeavyWindow-colour window.
+template <bool ASYNC>
+__device__ int d2_vertex_block(const KParams &p, const int32_t *R, int32_t v, int64_t beg, int64_t end, int cv,
+                               bool test, D2Shared &sh, int lane, bool &defective, long long &mb)
+{
+    const int wid = threadIdx.x >> 5;
+    defective = false;
+    for (int base = 1;; base += kHeavyWindow) {
+        __syncthreads();
+        for (int w = threadIdx.x; w < kHeavyWords; w += blockDim.x) sh.block_bm[w] = 0u;
+        if (threadIdx.x == 0) sh.first_free = INT_MAX;
+        __syncthreads();
+        const bool first = base == 1;
+        long long e = 0;
+        const bool hit = d2_read<ASYNC>(p, R, v, beg + 32 * wid, end, 32 * kWarps, cv, test && first, base,
+                                        kHeavyWindow, sh.block_bm, lane, e);
+        if (first) {
+            mb += 8 * e;
+            defective = __syncthreads_or(hit) != 0;
+            if (test && !defective) return cv;
+        } else {
+            __syncthreads();
+        }
+        for (int w = threadIdx.x; w < kHeavyWords; w += blockDim.x) {
+            const uint32_t x = sh.block_bm[w];
+            if (x != 0xffffffffu) {
+                atomicMin(&sh.first_free, w * 32 + __ffs(~x) - 1);
+                break;  // this thread's later words hold larger colours
+            }
+        }
+        __syncthreads();
+        const int f = sh.first_free;
+        if (f != INT_MAX) return base + f;
+    }
+}
+
 enum D2Op : int { D2_FF = 0, D2_RSOC = 1 };
 
-// One pass over cnt worklist entries (in == null: the ids 0..cnt-1), tiles
-// of 32 entries claimed per warp from *claim.  D2_FF: round 0 of the
-// asynchronous schedule, First-Fit for every vertex.  D2_RSOC: one
-// iteration of Algorithm 3's while-loop; defective vertices are recoloured
-// and pushed onto out (count in *pushed).  mb: the byte model, per lane.
+// Warps' share of one pass over cnt worklist entries (in == null: the ids
+// 0..cnt-1, heavy vertices skipped: the blocks take them), tiles of 32
+// entries claimed per warp from *claim.  D2_FF: round 0 of the asynchronous
+// schedule, First-Fit for every vertex.  D2_RSOC: one iteration of
+// Algorithm 3's while-loop; defective vertices are recoloured and pushed
+// onto out (count in *pushed).  mb: the byte model, per lane.
 template <bool ASYNC, int OP>
 __device__ void d2_pass(const KParams &p, const int32_t *in, int cnt, const int32_t *R, int32_t *W, int32_t *out,
                         int *claim, int *pushed, uint32_t *bm, int lane, long long &mb)
 {
+    const uint32_t *heavy = reinterpret_cast<const uint32_t *>(p.done);
     for (;;) {
         int t0 = 0;
         if (lane == 0) t0 = atomicAdd(claim, 32);
         t0 = __shfl_sync(FULL_MASK, t0, 0);
         if ((unsigned)t0 >= (unsigned)cnt) break;  // (a wrapped counter reads as past the end)
         const long long i = (long long)t0 + lane;
-        const int32_t mine = i < cnt ? (in ? __ldcg(in + i) : (int32_t)i) : -1;
-        const int m = min(32, cnt - t0);
+        int32_t mine = i < cnt ? (in ? __ldcg(in + i) : (int32_t)i) : -1;
+        if (!in && mine >= 0 && ((__ldcg(heavy + (mine >> 5)) >> (mine & 31)) & 1u)) mine = -1;
+        // the tile's row bounds and own colours, one vertex per lane (a
+        // vertex's colour changes only when its own warp recolours it)
+        int my_beg = 0, my_end = 0, my_cv = 0;
+        if (mine >= 0) {
+            my_beg = __ldg(p.row_ptr + mine);
+            my_end = __ldg(p.row_ptr + mine + 1);
+            if (OP == D2_RSOC) my_cv = ld_color<ASYNC>(R + mine);
+        }
         bool my_def = false;
-        for (int j = 0; j < m; ++j) {
+        unsigned todo = __ballot_sync(FULL_MASK, mine >= 0);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
             const int32_t v = __shfl_sync(FULL_MASK, mine, j);
-            const int64_t beg = __ldg(p.row_ptr + v), end = __ldg(p.row_ptr + v + 1);
+            const int64_t beg = __shfl_sync(FULL_MASK, my_beg, j), end = __shfl_sync(FULL_MASK, my_end, j);
             bool d = false;
             if (OP == D2_FF) {
                 const int k = d2_vertex<ASYNC>(p, R, v, beg, end, 0, false, bm, lane, d, mb);
@@ -173,7 +244,7 @@ __device__ void d2_pass(const KParams &p, const int32_t *in, int cnt, const int3
                     mb += 8 + 16 * (end - beg) + 4;
                 }
             } else {
-                const int cv = ld_color<ASYNC>(R + v);
+                const int cv = __shfl_sync(FULL_MASK, my_cv, j);
                 const int k = d2_vertex<ASYNC>(p, R, v, beg, end, cv, true, bm, lane, d, mb);
                 if (lane == 0) {
                     if (!ASYNC || d) st_color<ASYNC>(W + v, k);  // deterministic: every inspected vertex
@@ -194,48 +265,140 @@ __device__ void d2_pass(const KParams &p, const int32_t *in, int cnt, const int3
     }
 }
 
-template <bool ASYNC>
-__global__ void __launch_bounds__(kBlock) color_d2_kernel(KParams p)
+// Blocks' share of the same pass: the heavy vertices hin[0..hcnt), one
+// block each, claimed from *claim.  listed: the entries come from a
+// worklist (the byte model's 4 per entry).  Defective vertices go onto hout
+// (count in *hpushed): they stay heavy.
+template <bool ASYNC, int OP>
+__device__ void d2_heavy_pass(const KParams &p, const int32_t *hin, int hcnt, bool listed, const int32_t *R,
+                              int32_t *W, int32_t *hout, int *claim, int *hpushed, D2Shared &sh, int lane,
+                              long long &mb)
 {
-    __shared__ uint32_t bms[kWarps][kD2Words];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) sh.item = atomicAdd(claim, 1);
+        __syncthreads();
+        const int it = sh.item;
+        if ((unsigned)it >= (unsigned)hcnt) break;
+        const int32_t v = __ldcg(hin + it);
+        const int64_t beg = __ldg(p.row_ptr + v), end = __ldg(p.row_ptr + v + 1);
+        bool d = false;
+        if (OP == D2_FF) {
+            const int k = d2_vertex_block<ASYNC>(p, R, v, beg, end, 0, false, sh, lane, d, mb);
+            if (threadIdx.x == 0) {
+                st_color<ASYNC>(W + v, k);
+                mb += 8 + 16 * (end - beg) + 4;
+            }
+        } else {
+            const int cv = ld_color<ASYNC>(R + v);
+            const int k = d2_vertex_block<ASYNC>(p, R, v, beg, end, cv, true, sh, lane, d, mb);
+            if (threadIdx.x == 0) {
+                if (!ASYNC || d) st_color<ASYNC>(W + v, k);
+                mb += (listed ? 4 : 0) + 8 + 4 + 16 * (end - beg) + (d ? 8 : 0);
+                if (d) __stcg(hout + atomicAdd(hpushed, 1), v);
+            }
+        }
+    }
+}
+
+// Heavy vertices: two-hop entries (sum of the neighbours' degrees) above
+// p.d2_heavy.  One thread per vertex, a warp per 32 consecutive ids writes
+// one word of the flag bitmap (p.done) and appends its heavy vertices to
+// p.hub_all.
+__device__ void d2_find_heavy(const KParams &p, DevState *st, int lane)
+{
+    uint32_t *flags = reinterpret_cast<uint32_t *>(p.done);
+    const long long gthreads = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < p.n; b += gthreads) {
+        const long long vi = b + threadIdx.x;
+        bool heavy = false;
+        if (vi < p.n) {
+            const int32_t v = (int32_t)vi;
+            const int beg = __ldg(p.row_ptr + v), end = __ldg(p.row_ptr + v + 1);
+            if (end - beg > p.d2_heavy) {
+                heavy = true;
+            } else {
+                long long s = 0;
+#pragma unroll 4
+                for (int k = beg; k < end; ++k) {
+                    const int32_t u = __ldg(p.col_idx + k);
+                    s += __ldg(p.row_ptr + u + 1) - __ldg(p.row_ptr + u);
+                    if (s > p.d2_heavy) {
+                        heavy = true;
+                        break;
+                    }
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, heavy);
+        const long long w0 = vi - lane;  // first id of this warp's 32 (a multiple of 32)
+        if (lane == 0 && w0 < p.n) flags[w0 >> 5] = m;
+        if (m) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&st->hub_all_count, __popc(m));
+            pos = __shfl_sync(FULL_MASK, pos, 0);
+            if (heavy) __stcg(p.hub_all + pos + __popc(m & ((1u << lane) - 1u)), (int32_t)vi);
+        }
+    }
+}
+
+template <bool ASYNC>
+__global__ void __launch_bounds__(kBlock, GC_D2_MIN_BLOCKS) color_d2_kernel(KParams p)
+{
+    __shared__ D2Shared sh;
     DevState *st = p.st;
     const int lane = threadIdx.x & 31;
-    uint32_t *bm = bms[threadIdx.x >> 5];
+    uint32_t *bm = sh.warp_bm[threadIdx.x >> 5];
     const unsigned nbl = gridDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     long long mb = 0;
     if (lead) st->t_start = global_timer();
 
-    // round 0: every vertex colour 1 (deterministic), or uncoloured and then
-    // First-Fit over D2(v) in place (asynchronous)
+    // prologue: heavy vertices; round 0: every vertex colour 1
+    // (deterministic), or uncoloured and then First-Fit over D2(v) in place
+    // (asynchronous)
+    d2_find_heavy(p, st, lane);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += gthreads)
         __stcg(p.cA + i, ASYNC ? 0 : 1);
     if (!ASYNC && lead) mb += 4ll * p.n;
     grid_sync(st, nbl);
+    const int nheavy = ld_volatile(&st->hub_all_count);
     if (ASYNC && !(ld_volatile(&st->error) & GC_EW_TIMEOUT)) {
         d2_pass<true, D2_FF>(p, nullptr, p.n, p.cA, p.cA, nullptr, &st->pass_hub[0], nullptr, bm, lane, mb);
+        d2_heavy_pass<true, D2_FF>(p, p.hub_all, nheavy, false, p.cA, p.cA, nullptr, &st->d2_hclaim0, nullptr, sh,
+                                   lane, mb);
         grid_sync(st, nbl);
     }
     if (lead) st->stamp[0] = global_timer();
 
-    const int32_t *in = nullptr;  // iteration 1: U = V
-    int cnt = p.n;
+    // iteration 1: U = V (warps take the light vertices, blocks the heavy
+    // list); later: the light and heavy vertices recoloured the iteration
+    // before
+    const int32_t *in = nullptr, *hin = p.hub_all;
+    int cnt = p.n, hcnt = nheavy;
     for (int it = 1; !(ld_volatile(&st->error) & GC_EW_TIMEOUT); ++it) {
+        const int r = it & (kRing - 1);
         const int32_t *R = (ASYNC || (it & 1)) ? p.cA : p.cB;
         int32_t *W = (ASYNC || !(it & 1)) ? p.cA : p.cB;
-        int32_t *out = p.wl[it & 1];
-        d2_pass<ASYNC, D2_RSOC>(p, in, cnt, R, W, out, &st->pass_tile[it & (kRing - 1)],
-                                &st->hub_count[it & (kRing - 1)], bm, lane, mb);
+        d2_pass<ASYNC, D2_RSOC>(p, in, cnt, R, W, p.wl[it & 1], &st->pass_tile[r], &st->hub_count[r], bm, lane, mb);
+        if (hcnt > 0)
+            d2_heavy_pass<ASYNC, D2_RSOC>(p, hin, hcnt, in != nullptr, R, W, p.hub[it & 1], &st->d2_hclaim[r],
+                                          &st->d2_hcount[r], sh, lane, mb);
         // counters of iteration it+2: their last readers passed the barrier
         // that ended iteration it-1
         if (lead) {
-            st->pass_tile[(it + 2) & (kRing - 1)] = 0;
-            st->hub_count[(it + 2) & (kRing - 1)] = 0;
+            const int r2 = (it + 2) & (kRing - 1);
+            st->pass_tile[r2] = 0;
+            st->hub_count[r2] = 0;
+            st->d2_hcount[r2] = 0;
+            st->d2_hclaim[r2] = 0;
         }
         grid_sync(st, nbl);
         if (ld_volatile(&st->error) & GC_EW_TIMEOUT) break;
-        const int size = ld_volatile(&st->hub_count[it & (kRing - 1)]);
+        const int light = ld_volatile(&st->hub_count[r]);
+        const int hvy = ld_volatile(&st->d2_hcount[r]);
+        const int size = light + hvy;
         if (lead) {
             st->rounds = it;
             st->conflicts += (unsigned long long)size;
@@ -252,8 +415,10 @@ __global__ void __launch_bounds__(kBlock) color_d2_kernel(KParams p)
                     __stcg(p.cA + i, __ldcg(W + i));
             break;
         }
-        in = out;
-        cnt = size;
+        in = p.wl[it & 1];
+        cnt = light;
+        hin = p.hub[it & 1];
+        hcnt = hvy;
     }
 
     if (p.stats_bitmap) {

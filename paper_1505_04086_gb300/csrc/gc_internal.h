@@ -105,6 +105,9 @@ struct DevState {
     unsigned long long stamp[kStamps];  // [0]: end of round 0, [k]: end of iteration k
     int round_head[kStamps];         // |L| of iterations 1..kStamps (copied back with the state)
     unsigned int stats_done;         // colour-statistics blocks finished
+    int d2_hcount[kRing];            // distance-2: heavy vertices pushed per iteration
+    int d2_hclaim[kRing];            // distance-2: heavy vertices claimed per iteration
+    int d2_hclaim0;                  // distance-2: heavy vertices claimed in round 0
 };
 
 struct KParams {
@@ -150,6 +153,7 @@ struct KParams {
     int32_t n_touched;
     int64_t *pitems;           // round 0: (graph, warp, group size) of each grouped warp
     int32_t pitems_cap;        // its capacity (>= the grid's warps)
+    int32_t d2_heavy;          // distance 2: two-hop entries above which a block inspects a vertex
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

@@ -60,10 +60,16 @@ def ids(gs):
 GRAPHS = graphs()
 
 
+# two-hop sizes above which a block, not a warp, inspects a vertex: the
+# default, and thresholds low enough that the small graphs mix both paths
+HEAVY = {"default": None, "heavy64": {"d2_heavy": 64}, "heavy300": {"d2_heavy": 300}}
+
+
 @pytest.mark.parametrize("g", GRAPHS, ids=ids(GRAPHS))
 @pytest.mark.parametrize("tie", [0, HIGHER], ids=["lower", "higher"])
-def test_det_d2_matches_the_oracle_replay(ctx, g, tie):
-    rc, col, st = run(ctx, g, D2 | tie | gc.GC_CHECKED)
+@pytest.mark.parametrize("heavy", list(HEAVY))
+def test_det_d2_matches_the_oracle_replay(ctx, g, tie, heavy):
+    rc, col, st = run(ctx, g, D2 | tie | gc.GC_CHECKED, HEAVY[heavy])
     ref = O.rsoc_det_d2(g, O.TIE_HIGHER_KEEPS if tie else O.TIE_LOWER_KEEPS)
     assert rc == gc.GC_OK, gc.gc_strerror(rc)
     assert np.array_equal(col, ref.colors), f"first diff at {np.nonzero(col != ref.colors)[0][:5]}"
@@ -76,9 +82,10 @@ def test_det_d2_matches_the_oracle_replay(ctx, g, tie):
         assert O.check_d2(g, col) == 0
 
 
-def test_det_d2_larger_power_law_graph(ctx):
+@pytest.mark.parametrize("heavy", [None, 2048])
+def test_det_d2_larger_power_law_graph(ctx, heavy):
     g = I.rmat(11, ef=8)  # hubs of degree ~600: two-hop rows of many warps' width
-    rc, col, st = run(ctx, g, D2)
+    rc, col, st = run(ctx, g, D2, {"d2_heavy": heavy} if heavy else None)
     ref = O.rsoc_det_d2(g)
     assert rc == gc.GC_OK
     assert np.array_equal(col, ref.colors)
@@ -98,8 +105,9 @@ def test_det_d2_round_cap_returns_the_colouring_at_the_cap(ctx, cap):
 
 @pytest.mark.parametrize("g", GRAPHS, ids=ids(GRAPHS))
 @pytest.mark.parametrize("tie", [0, HIGHER], ids=["lower", "higher"])
-def test_async_d2_is_a_distance2_colouring(ctx, g, tie):
-    rc, col, st = run(ctx, g, D2 | ASYNC | tie | gc.GC_CHECKED)
+@pytest.mark.parametrize("heavy", list(HEAVY))
+def test_async_d2_is_a_distance2_colouring(ctx, g, tie, heavy):
+    rc, col, st = run(ctx, g, D2 | ASYNC | tie | gc.GC_CHECKED, HEAVY[heavy])
     assert rc == gc.GC_OK, gc.gc_strerror(rc)
     assert O.check_d2(g, col) == 0
     if g.n:
@@ -109,14 +117,22 @@ def test_async_d2_is_a_distance2_colouring(ctx, g, tie):
         assert col.max() <= max(ff, 1) * 2 + 1, (col.max(), ff)
 
 
-def test_async_d2_beyond_one_colour_window(ctx):
+@pytest.mark.parametrize("n,heavy", [(2300, None), (2300, 1000)])
+def test_async_d2_beyond_one_colour_window(ctx, n, heavy):
     # the square of a star is complete: every vertex needs its own colour, so
-    # First-Fit runs past the 2048-colour window
-    n = 2300
+    # First-Fit runs past the 2048-colour window of a warp (every vertex
+    # light), or fills 2300 colours of a block's window (every vertex heavy)
     g = I.from_edges(n, [(0, i) for i in range(1, n)])
-    rc, col, st = run(ctx, g, D2 | ASYNC | gc.GC_CHECKED)
+    rc, col, st = run(ctx, g, D2 | ASYNC | gc.GC_CHECKED, {"d2_heavy": heavy} if heavy else None)
     assert rc == gc.GC_OK, gc.gc_strerror(rc)
     assert np.array_equal(np.sort(col), np.arange(1, n + 1))
+
+
+def test_async_d2_power_law_validity_at_size(ctx):
+    g = I.rmat(16)  # two-hop neighbourhoods up to ~1.4M entries: the block path
+    rc, col, st = run(ctx, g, D2 | ASYNC | gc.GC_CHECKED)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    assert O.check_d2(g, col) == 0
 
 
 def test_async_d2_mesh_validity_at_size(ctx):
