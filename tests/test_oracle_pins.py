@@ -472,6 +472,20 @@ def test_d2_closed_forms():
 
 
 @pytest.mark.parametrize("make", D2_GRAPHS)
+def test_d2_check_is_validity_on_the_square(make):
+    # brute force over the explicit G^2: every edge of G^2 joins two colours
+    # that differ, and every vertex is coloured
+    g = make()
+    sq = square(g)
+    rng = np.random.default_rng(3)
+    for trial in range(30):
+        c = rng.integers(0 if trial % 5 == 0 else 1, 5, g.n).astype(np.int32)
+        ok = bool(np.all(c >= 1)) and all(c[v] != c[u] for v in range(sq.n)
+                                          for u in sq.col_idx[sq.row_ptr[v]:sq.row_ptr[v + 1]])
+        assert (O.check_d2(g, c) == 0) == ok, trial
+
+
+@pytest.mark.parametrize("make", D2_GRAPHS)
 @pytest.mark.parametrize("tie", [O.TIE_LOWER_KEEPS, O.TIE_HIGHER_KEEPS])
 def test_d2_replay_is_the_replay_of_the_square(make, tie):
     # Same colours, iterations, conflicts and round sizes as the distance-1
