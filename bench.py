@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--mode", default="rsoc_async", help="batch/serve workloads: colouring mode")
     ap.add_argument("--graphs", type=int, default=BATCH_G, help="batch workload: number of graphs")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: default options, no autotuning")
+    ap.add_argument("--opts", default=None,
+                    help="single graph: headline options as JSON (gc_opts fields) instead of the autotuner's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline mode only")
     return ap.parse_args()
@@ -75,23 +77,27 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+COLOR_KERNEL_SOURCES = ("gc_kernels.cu", "gc_device.cuh", "gc_internal.h")
+D2_KERNEL_SOURCES = ("gc_d2.cu", "gc_device.cuh", "gc_internal.h")
+
+
+def kernel_source_hash(files=COLOR_KERNEL_SOURCES):
     h = hashlib.sha256()
-    for f in ("gc_kernels.cu", "gc_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1505_04086_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, mode_name):
-    """DRAM bytes per launch of the colouring kernel from a committed ncu
+def recorded_traffic(workload, mode_name, files=COLOR_KERNEL_SOURCES):
+    """DRAM bytes per launch of a colouring kernel from a committed ncu
     summary, if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[f"{workload}/{mode_name}"]
-        if e.get("kernel_sha") != kernel_source_hash():
+        if e.get("kernel_sha") != kernel_source_hash(files):
             return None
         return int(e["dram_bytes_per_launch"])
     except Exception:
@@ -231,9 +237,13 @@ def run_ours(args, ws, rank, local):
     # options from the library's autotuner, chosen before the timed region
     tune_col = torch.empty(g.n, dtype=torch.int32, device=dev)
     t_tune = time.perf_counter()
-    rc, tune = gc.gc_autotune(ctx.handle, rp, ci, g.n, g.nnz, MODES[head], tune_col, reps=3)
-    if rc != gc.GC_OK:
-        raise RuntimeError(gc.gc_strerror(rc))
+    if args.opts:
+        tune = {"best": {k: int(v) for k, v in json.loads(args.opts).items()}, "best_ms": 0.0,
+                "default_ms": 0.0, "evaluated": 0}
+    else:
+        rc, tune = gc.gc_autotune(ctx.handle, rp, ci, g.n, g.nnz, MODES[head], tune_col, reps=3)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
     t_tune = time.perf_counter() - t_tune
     opts = tune["best"]
     del tune_col
@@ -367,6 +377,7 @@ def run_ours(args, ws, rank, local):
                  "achieved_gbs": round(d2_mb / (d2_kms / 1e3) / 1e9, 1),
                  "frac": round(d2_mb / (d2_kms / 1e3) / 1e9 / peak, 4),
                  "kernel": "gc::color_d2_kernel<async>", "checked": "GC_CHECKED (distance 2) on the device",
+                 "traffic": recorded_traffic(args.workload, head + "_d2", D2_KERNEL_SOURCES),
                  "steps": k}
 
     # --- end to end through the C ABI with host buffers ----------------------
@@ -418,7 +429,8 @@ def run_ours(args, ws, rank, local):
         "incremental": incremental,
         "distance2": dist2,
         "autotune": {"opts": opts, "best_ms": round(tune["best_ms"], 4), "default_ms": round(tune["default_ms"], 4),
-                     "evaluated": tune["evaluated"], "seconds": round(t_tune, 2)},
+                     "evaluated": tune["evaluated"], "seconds": round(t_tune, 2),
+                     "source": "--opts" if args.opts else "gc_autotune"},
         "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "cpu_openmp": cpu_omp,
         "gpu_launches": launches_per_call * args.steps, "clocks": clocks, "modes": extra,
         "wall_s": round(wall, 3),
