@@ -49,23 +49,27 @@ struct D2Shared {
     int item;
 };
 
-// Mark colour c in the window of colours [base, base + window).
-__device__ __forceinline__ void d2_mark(uint32_t *bm, int c, int base, int window)
+// Mark colour c in the window of colours [base, base + window): the first
+// 64 colours of the window in the lane's register mask `low` (OR-reduced
+// over the warp afterwards), the rest in the shared-memory bitmap bm.
+__device__ __forceinline__ void d2_mark(uint32_t *bm, unsigned long long &low, int c, int base, int window)
 {
     const unsigned o = (unsigned)(c - base);
-    if (o < (unsigned)window) atomicOr(bm + (o >> 5), 1u << (o & 31));
+    if (o < 64u) low |= 1ull << o;
+    else if (o < (unsigned)window) atomicOr(bm + (o >> 5), 1u << (o & 31));
 }
 
 // One read of this warp's share of D2(v) in the colour buffer R: the
 // neighbours at entries kfirst, kfirst + kstride, ... (chunks of 32) of v's
 // row, which ends at `end`, and their rows.  Marks every colour in the
-// window [base, base + window); returns (per lane) whether a vertex read on
-// v's tie side holds colour cv (only if test).  entries: the lane's share of
-// the two-hop entries read (the byte model's 8 per entry of a neighbour's
-// row).
+// window [base, base + window) (its first 64 colours in the lane's mask
+// low); returns (per lane) whether a vertex read on v's tie side holds
+// colour cv (only if test).  entries: the lane's share of the two-hop
+// entries read (the byte model's 8 per entry of a neighbour's row).
 template <bool ASYNC>
 __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t kfirst, int64_t end, int kstride,
-                        int cv, bool test, int base, int window, uint32_t *bm, int lane, long long &entries)
+                        int cv, bool test, int base, int window, uint32_t *bm, unsigned long long &low, int lane,
+                        long long &entries)
 {
     bool hit = false;
     for (int64_t k0 = kfirst; k0 < end; k0 += kstride) {
@@ -76,7 +80,7 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t k
             ub = __ldg(p.row_ptr + u);
             du = __ldg(p.row_ptr + u + 1) - ub;
             const int cu = ld_color<ASYNC>(R + u);
-            d2_mark(bm, cu, base, window);
+            d2_mark(bm, low, cu, base, window);
             if (test && cu == cv && on_tie_side(p.tie, u, v)) hit = true;
         }
         entries += du;
@@ -113,7 +117,7 @@ __device__ bool d2_read(const KParams &p, const int32_t *R, int32_t v, int64_t k
             for (int j = 0; j < kD2Unroll; ++j) {
                 if (w[j] >= 0 && w[j] != v) {
                     const int cw = ld_color<ASYNC>(R + w[j]);
-                    d2_mark(bm, cw, base, window);
+                    d2_mark(bm, low, cw, base, window);
                     if (test && cw == cv && on_tie_side(p.tie, w[j], v)) hit = true;
                 }
             }
@@ -139,14 +143,18 @@ __device__ int d2_vertex(const KParams &p, const int32_t *R, int32_t v, int64_t 
         __syncwarp();
         const bool first = base == 1;
         long long e = 0;
-        const bool hit = d2_read<ASYNC>(p, R, v, beg, end, 32, cv, test && first, base, kD2Window, bm, lane, e);
+        unsigned long long low = 0;
+        const bool hit =
+            d2_read<ASYNC>(p, R, v, beg, end, 32, cv, test && first, base, kD2Window, bm, low, lane, e);
         if (first) {
             mb += 8 * e;
             defective = __any_sync(FULL_MASK, hit);
             if (test && !defective) return cv;
         }
+        const unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)low);
+        const unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(low >> 32));
         __syncwarp();
-        const uint32_t w0 = bm[lane], w1 = bm[lane + 32];
+        const uint32_t w0 = bm[lane] | (lane == 0 ? lo : (lane == 1 ? hi : 0u)), w1 = bm[lane + 32];
         unsigned m = __ballot_sync(FULL_MASK, w0 != 0xffffffffu);
         if (m) {
             const int l = __ffs(m) - 1;
@@ -178,8 +186,13 @@ __device__ int d2_vertex_block(const KParams &p, const int32_t *R, int32_t v, in
         __syncthreads();
         const bool first = base == 1;
         long long e = 0;
+        unsigned long long low = 0;
         const bool hit = d2_read<ASYNC>(p, R, v, beg + 32 * wid, end, 32 * kWarps, cv, test && first, base,
-                                        kHeavyWindow, sh.block_bm, lane, e);
+                                        kHeavyWindow, sh.block_bm, low, lane, e);
+        const unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)low);
+        const unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(low >> 32));
+        if (lane == 0 && lo) atomicOr(&sh.block_bm[0], lo);
+        if (lane == 0 && hi) atomicOr(&sh.block_bm[1], hi);
         if (first) {
             mb += 8 * e;
             defective = __syncthreads_or(hit) != 0;
