@@ -412,6 +412,9 @@ def run_ours(args, ws, rank, local):
         cpu, ff_colors = cpu_baseline(g, budget_s=12.0)
         cpu_omp = host_openmp(gc, g)
 
+    if ff_colors:
+        for v in extra.values():
+            v["colors_vs_ff"] = round(v["colors"] / ff_colors, 4)
     launches_per_call = 1  # color_kernel (colour statistics at its end)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": ws,

@@ -85,7 +85,10 @@ enum {
                                     degree > t1, then the rest, each tier taken
                                     through round 0 and its repair rounds before
                                     the next (later tiers are uncoloured while
-                                    an earlier one is repaired) */
+                                    an earlier one is repaired).  Close to
+                                    largest-first order: on power-law graphs
+                                    fewer colours than the plain asynchronous
+                                    schedule (t2 defaults to 4096 here) */
     GC_FF_KEEPERS = 512,         /* with GC_SCHED_ASYNC, GC_ALG_RSOC and
                                     GC_TIE_LOWER_KEEPS only (else GC_ERR_ARG;
                                     not with GC_REPAIR_SNAPSHOT): a vertex's
@@ -187,7 +190,8 @@ typedef struct {
     int32_t max_rounds;          /* iteration cap; 0 = n+1 */
     int32_t t1;                  /* degree <= t1: thread per vertex (<= 62); 0 = 32 */
     int32_t t2;                  /* t1 < degree <= t2: warp per vertex; above:
-                                    block per vertex (<= 4096); 0 = 2048 */
+                                    block per vertex (<= 4096); 0 = 2048
+                                    (4096 with GC_TIERS) */
     int32_t tile;                /* worklist entries a warp claims at once
                                     (multiple of 32, <= 4096); 0 = 64 */
     int32_t blocks_per_sm;       /* resident blocks per SM; 0 = occupancy max */

@@ -43,14 +43,14 @@ struct Resolved {
     int32_t max_rounds, t1, t2, tile, tail, blocks_per_sm, window, d2_heavy;
 };
 
-int resolve_opts(const gc_opts *o, int64_t n, Resolved &r)
+int resolve_opts(const gc_opts *o, int64_t n, uint32_t mode, Resolved &r)
 {
     gc_opts d;
     memset(&d, 0, sizeof d);
     if (!o) o = &d;
     r.max_rounds = o->max_rounds > 0 ? o->max_rounds : (int32_t)std::min<int64_t>(n + 1, INT32_MAX);
     r.t1 = o->t1 > 0 ? o->t1 : 32;
-    r.t2 = o->t2 > 0 ? o->t2 : 2048;
+    r.t2 = o->t2 > 0 ? o->t2 : gc::default_t2(mode);
     r.tile = o->tile > 0 ? o->tile : 64;
     r.tail = o->tail > 0 ? o->tail : (o->tail < 0 ? -1 : 2048);
     r.blocks_per_sm = o->blocks_per_sm;
@@ -217,7 +217,7 @@ int color_batch_impl(gc_ctx *c, int32_t G, int64_t total_n, int64_t total_nnz, c
     if (total_n > 0 && !colors_out) return GC_ERR_ARG;
     Resolved r;
     // The cap applies per graph; every graph's own bound is below total_n + 1.
-    int rc = resolve_opts(opts, total_n, r);
+    int rc = resolve_opts(opts, total_n, mode, r);
     if (rc != GC_OK) return rc;
     c->last.pending = false;
     c->last.n = (int32_t)total_n;
@@ -381,7 +381,7 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
     Resolved r;
-    int rc = resolve_opts(opts, n, r);
+    int rc = resolve_opts(opts, n, mode, r);
     if (rc != GC_OK) return rc;
     c->last.pending = false;
     c->last.n = n;
@@ -419,7 +419,7 @@ int gc_recolor_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint3
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
     if (n_touched > 0 && !touched) return GC_ERR_ARG;
     Resolved r;
-    int rc = resolve_opts(opts, n, r);
+    int rc = resolve_opts(opts, n, mode, r);
     if (rc != GC_OK) return rc;
     c->last.pending = false;
     c->last.n = n;

@@ -12,6 +12,11 @@ namespace gc {
 
 constexpr int kRoundSizesDev = 65536;  // per-iteration |L| kept on the device
 
+// Default warp/block degree split.  With GC_TIERS it is also the first
+// tier's boundary: fewer, larger hubs coloured together keep a dense core's
+// concurrent First-Fit choices (and so the colour count) down.
+inline int32_t default_t2(uint32_t mode) { return (mode & GC_TIERS) ? 4096 : 2048; }
+
 struct Buf {
     void *p = nullptr;
     size_t bytes = 0;

@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "gc.h"
+#include "gc_ctx.h"
 #include "gc_internal.h"
 
 namespace {
@@ -114,7 +115,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
     const int32_t max_rounds = o.max_rounds > 0 ? o.max_rounds : n + 1;
-    const int32_t t1 = o.t1 > 0 ? o.t1 : 32, t2 = o.t2 > 0 ? o.t2 : 2048, tile = o.tile > 0 ? o.tile : 64;
+    const int32_t t1 = o.t1 > 0 ? o.t1 : 32, t2 = o.t2 > 0 ? o.t2 : gc::default_t2(mode), tile = o.tile > 0 ? o.tile : 64;
     const int32_t tail = o.tail > 0 ? o.tail : (o.tail < 0 ? -1 : 2048);
     if (t1 > gc::kT1Max || t2 > gc::kT2Max || t1 > t2 || tile % 32 != 0 || tile > 4096 ||
         o.blocks_per_sm < 0 || o.window < -1)

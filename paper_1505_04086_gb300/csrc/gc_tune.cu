@@ -92,7 +92,7 @@ int tune(gc_ctx *ctx, int reps, uint32_t mode, gc_tune_result *out, Run run)
     gc_opts best;  // the library defaults, spelled out
     memset(&best, 0, sizeof best);
     best.t1 = 32;
-    best.t2 = 2048;
+    best.t2 = gc::default_t2(mode);
     best.tile = 64;
     best.tail = 2048;
     float best_ms = 0.f;
