@@ -499,10 +499,10 @@ struct Shared {
     } slot[kWarps][2];
     uint32_t warp_bm[kWarps][kWarpBmWords];
     uint32_t hub_bm[kHubBmWords];
+    int found;                               // detect_block: a conflict was seen
     int first;
     int tcount;
     int claim;
-    int pad;
 };
 
 // Block-wide First-Fit over the neighbours u <= vmax (see ff_thread), in
@@ -534,7 +534,10 @@ __device__ int ff_block(const KParams &p, int64_t beg, int deg, int32_t nbase, c
                 const int d = c[q] - base;
                 if (c[q] >= 0 && d >= 0 && d < kWin) atomicOr(&sh.hub_bm[d >> 5], 1u << (d & 31));
             }
-            if (!__syncthreads_or(threadIdx.x == kBlock - 1 ? (int)take[kBlockUnroll - 1] : 0)) break;
+            // A thread's entries rise with i in a sorted row: once one is
+            // past the row's end or vmax, so are all its later ones.  No
+            // barrier: every thread runs ahead on its own entries.
+            if (!take[kBlockUnroll - 1]) break;
         }
         if (base == 0 && t) atomicAdd(&sh.tcount, t);
         __syncthreads();
@@ -573,7 +576,7 @@ __device__ void push_clashes_block(const KParams &p, int32_t v, int64_t beg, int
 #pragma unroll
         for (int q = 0; q < kBlockUnroll; ++q)
             if (side[q] && c[q] == k) push_one<BATCH>(p, u[q], it);
-        if (!__syncthreads_or(threadIdx.x == kBlock - 1 ? (int)side[kBlockUnroll - 1] : 0)) break;
+        if (!side[kBlockUnroll - 1]) break;  // this thread's entries fell to v or below
     }
 }
 
@@ -585,7 +588,10 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
     const int tie = p.tie;
     bool def = false;
     int t = 0;
-    if (threadIdx.x == 0) sh.tcount = 0;
+    if (threadIdx.x == 0) {
+        sh.tcount = 0;
+        sh.found = 0;
+    }
     __syncthreads();
     for (int i0 = 0; i0 < deg; i0 += kBlock * kBlockUnroll) {
         int32_t u[kBlockUnroll];
@@ -607,11 +613,14 @@ __device__ bool detect_block(const KParams &p, int32_t v, int64_t beg, int64_t e
                 ++t;
                 def |= (c[q] == cv);
             }
-        // one barrier: bit 0 = the tie side goes on, bit 1 = a conflict was seen
-        const int flags = __syncthreads_or(((threadIdx.x == kBlock - 1 && side[kBlockUnroll - 1]) ? 1 : 0) |
-                                           (def ? 2 : 0));
-        if (tie != TIE_NONE && !(flags & 1)) break;
-        if ((flags & 2) && stop_early) break;
+        // No barrier per step: a thread's entries move away from v in a
+        // sorted row (up from the row start, or down from its end with
+        // higher-keeps ties), so once one leaves the tie side all its later
+        // ones do; a conflict found by any thread ends the others' scans
+        // through a shared flag.
+        if (def && stop_early) *(volatile int *)&sh.found = 1;
+        if (tie != TIE_NONE && !side[kBlockUnroll - 1]) break;
+        if (stop_early && *(volatile int *)&sh.found) break;
     }
     if (t) atomicAdd(&sh.tcount, t);
     const int any = __syncthreads_or((int)def);
