@@ -362,10 +362,11 @@ typedef struct {
  * Choose gc_opts for colouring this batch in `mode` by timing it: coordinate
  * descent from the defaults over t1 (largest degree coloured by one
  * thread), t2 (largest degree coloured by one warp; above it a block per
- * vertex), tile, blocks_per_sm and tail (window, which changes which graphs
- * are coloured in id order and so the colour counts, stays automatic); each
- * candidate's cost is the median of `reps` (1..64) runs' device time
- * (CUDA events), and at most two sweeps are made.  In GC_SCHED_ASYNC the
+ * vertex), tile and blocks_per_sm (searched as pairs: they interact) and
+ * tail (window, which changes which graphs are coloured in id order and so
+ * the colour counts, stays automatic); each candidate's cost is the median
+ * of `reps` (1..64) runs' device time (CUDA events), and at most three
+ * sweeps are made.  In GC_SCHED_ASYNC the
  * options change the colouring as well: a candidate is taken only if none of
  * its runs used more colours than the default options' runs did (unless
  * GC_NO_COLOR_STATS is set).  Synchronous (legacy

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "gc.h"
@@ -77,18 +78,21 @@ int tune(gc_ctx *ctx, int reps, uint32_t mode, gc_tune_result *out, Run run)
     const bool guard = (mode & GC_SCHED_ASYNC) && !(mode & GC_NO_COLOR_STATS);
     // The knobs (only those that leave the method's result alone: window,
     // which decides which graphs are coloured in id order, changes colour
-    // counts and is not tuned), each with its candidate values.
-    struct Knob {
-        int32_t gc_opts::*field;
-        std::vector<int32_t> values;
-    };
-    const std::vector<Knob> knobs = {
-        {&gc_opts::t1, {8, 16, 24, 32, 48, 62}},
-        {&gc_opts::t2, {128, 256, 512, 1024, 2048, 4096}},
-        {&gc_opts::tile, {32, 64, 128, 256, 512}},
-        {&gc_opts::blocks_per_sm, {1, 2, 0}},
-        {&gc_opts::tail, {-1, 256, 2048, 8192}},
-    };
+    // counts and is not tuned), each with its candidate settings.  Tile and
+    // blocks per SM are searched jointly: the work a warp claims at once and
+    // the number of warps resident trade against each other, so one often
+    // pays off only together with the other.
+    using Setting = std::vector<std::pair<int32_t gc_opts::*, int32_t>>;
+    std::vector<std::vector<Setting>> knobs;
+    knobs.push_back({});
+    for (int32_t v : {8, 16, 24, 32, 48, 62}) knobs.back().push_back({{&gc_opts::t1, v}});
+    knobs.push_back({});
+    for (int32_t v : {128, 256, 512, 1024, 2048, 4096}) knobs.back().push_back({{&gc_opts::t2, v}});
+    knobs.push_back({});
+    for (int32_t t : {32, 64, 128, 256, 512})
+        for (int32_t b : {1, 2, 0}) knobs.back().push_back({{&gc_opts::tile, t}, {&gc_opts::blocks_per_sm, b}});
+    knobs.push_back({});
+    for (int32_t v : {-1, 256, 2048, 8192}) knobs.back().push_back({{&gc_opts::tail, v}});
     gc_opts best;  // the library defaults, spelled out
     memset(&best, 0, sizeof best);
     best.t1 = 32;
@@ -100,16 +104,20 @@ int tune(gc_ctx *ctx, int reps, uint32_t mode, gc_tune_result *out, Run run)
     int rc = measure(best, best_ms, default_colors);
     if (rc != GC_OK) return rc;
     out->default_ms = best_ms;
-    // Coordinate descent from the defaults: two sweeps over the knobs, each
-    // knob set to its fastest value with the others held.
-    for (int sweep = 0; sweep < 2; ++sweep) {
+    // Coordinate descent from the defaults: up to three sweeps over the
+    // knobs, each knob set to its fastest setting with the others held.
+    for (int sweep = 0; sweep < 3; ++sweep) {
         bool moved = false;
-        for (const Knob &k : knobs) {
-            const int32_t cur = best.*(k.field);
-            for (int32_t v : k.values) {
-                if (v == cur) continue;
-                gc_opts o = best;
-                o.*(k.field) = v;
+        for (const auto &knob : knobs) {
+            const gc_opts start = best;
+            for (const Setting &st : knob) {
+                gc_opts o = start;
+                bool same = true;
+                for (const auto &fv : st) {
+                    same = same && (o.*(fv.first) == fv.second);
+                    o.*(fv.first) = fv.second;
+                }
+                if (same) continue;
                 if (o.t1 > o.t2) continue;  // thread bin above the warp bin
                 float ms = 0.f;
                 int colors = 0;
