@@ -162,9 +162,12 @@ typedef struct {
                                     (detection passes); 8 per adjacency entry
                                     read (index + colour): all entries for a
                                     (re)colouring, the tie side for a clean
-                                    detection; 4 per colour written and per
-                                    worklist push; 4 per vertex for a pass in
-                                    which nothing is coloured yet.  GC_DIST2:
+                                    detection; 4 (index only) for a neighbour
+                                    the asynchronous round 0 knows to be
+                                    uncoloured (in a tile not yet claimed); 4
+                                    per colour written and per worklist push;
+                                    4 per vertex for a pass in which nothing
+                                    is coloured yet.  GC_DIST2:
                                     per inspected vertex 4 (worklist entry,
                                     not in a pass over all of V) + 8 + 4 (own
                                     colour; not in the asynchronous round 0)

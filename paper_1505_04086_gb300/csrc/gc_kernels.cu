@@ -757,7 +757,8 @@ __device__ __forceinline__ int resolve_in_order(unsigned long long ext, unsigned
 template <class E, bool RING>
 __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cbase, int32_t v, int64_t beg,
                                    int64_t end, int32_t nbase, int32_t *C, long long &mb, uint32_t *bm, int lane,
-                                   int dmax, uint16_t *ring = nullptr, long long v0 = 0, bool skip_higher = false)
+                                   int dmax, uint16_t *ring = nullptr, long long v0 = 0, bool skip_higher = false,
+                                   int32_t unclaimed = INT32_MAX)
 {
     const int deg = (int)(end - beg);
     const int tie = p.tie;
@@ -786,7 +787,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // An ordered graph whose higher ids are all uncoloured (skip_higher)
     // gains nothing from the part of a row above v either.
     const bool keep = keepers || (RING && skip_higher);
-    int nread = 0;
+    int nread = 0, nskip = 0;
     PT_BEGIN(t_g);
     if (thr) {
         const auto row = ent.row(beg);
@@ -826,8 +827,15 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
                 for (int q = 0; q < kUnroll; ++q)
                     if (glob[q]) c[q] = ld_color<true>(C + u[q]);
             } else {
+                // Ids from `unclaimed` on belong to tiles no warp has claimed
+                // yet: uncoloured, so their colours are not read (what the
+                // read would return, taken a moment earlier).
 #pragma unroll
-                for (int q = 0; q < kUnroll; ++q) c[q] = outside[q] ? ld_color<true>(C + u[q]) : 0;
+                for (int q = 0; q < kUnroll; ++q) {
+                    const bool skip = outside[q] && u[q] >= unclaimed;
+                    nskip += skip;
+                    c[q] = (outside[q] && !skip) ? ld_color<true>(C + u[q]) : 0;
+                }
             }
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
@@ -845,7 +853,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     PT_END(p.st, 7, t_r);
     if (thr) {
         st_color<true>(C + v, mine);
-        mb += 8 + 8ll * nread + 4;
+        mb += 8 + 8ll * nread - 4ll * nskip + 4;  // index only for the unread colours
     }
     __syncwarp();
     PT_BEGIN(t_mid);
@@ -1395,6 +1403,13 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
     // round-0 tentative pass).
     const long long nchunks = ordered ? *(volatile long long *)&st->n_uchunks : (n + 31) / 32;
     const long long ntiles = (nchunks + cpt - 1) / cpt;
+    // One graph, tiles claimed in id order, lower ids keep their colour, no
+    // vertex coloured before the tiles (hubs, earlier tiers): every id past
+    // the claimed tiles is uncoloured, and as a higher neighbour its colour
+    // is not needed for the suspect test either.
+    const bool skip_unclaimed = ordered && !BATCH && p.tie == TIE_LOWER &&
+                                !(p.mode & (GC_TIERS | GC_FF_KEEPERS)) && window <= 0 &&
+                                __ldcg(&p.gstat[0].hubs) == 0u;
 
     int t = 0;
     if (lane == 0) t = atomicAdd(claim, 1);
@@ -1438,12 +1453,20 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
         PT_BEGIN(t_proc);
         const int32_t v = cur.deg >= 0 ? (int32_t)(cb + lane) : -1;
         const int64_t end = cur.beg + (cur.deg > 0 ? cur.deg : 0);
+        int32_t unclaimed = INT32_MAX;
+        if (skip_unclaimed) {
+            // the tiles past this warp's latest claim were unclaimed when it
+            // made that claim
+            const long long first_free = ((long long)ntile + 1) * cpt * 32;
+            if (first_free < n) unclaimed = (int32_t)first_free;
+        }
         bool sus = false;
         if (staged) {
             const StagedEnts ent{sh.seg[wid][slot], soff};
             if (ordered)
                 sus = chunk_tent_ordered<StagedEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
-                                                            sh.warp_bm[wid], lane, in.dmax);
+                                                            sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
+                                                            unclaimed);
             else
                 chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, v, cur.beg, end, cur.nbase, cur.g, R, W,
                                         push, mb, lane, wid);
@@ -1451,7 +1474,8 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
             const GlobalEnts ent{p.col_idx};
             if (ordered)
                 sus = chunk_tent_ordered<GlobalEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
-                                                            sh.warp_bm[wid], lane, in.dmax);
+                                                            sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
+                                                            unclaimed);
             else
                 chunk_ops<ASYNC, BATCH>(p, sh, ent, op, it, true, in.dmax, v, cur.beg, end, cur.nbase, cur.g, R, W,
                                         push, mb, lane, wid);
