@@ -539,6 +539,21 @@ int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int3
  * built without OpenMP). */
 int gc_host_threads(void);
 
+/* ---- failure path ------------------------------------------------------ */
+
+/*
+ * Check of the bounded wait that every persistent kernel's grid barrier
+ * uses: a cooperative launch on `device` (2 blocks) whose barrier waits for
+ * one block more than the grid holds, an arrival that never comes.  After
+ * timeout_ms (1..10000) the wait gives up, the device error word receives
+ * GC_EW_TIMEOUT (copied to *error_word_out if not NULL) and the kernel
+ * returns; the CUDA context stays usable.  Synchronous.  Returns
+ * GC_ERR_TIMEOUT when the wait ran out as it should, GC_OK if it did not,
+ * GC_ERR_ARG or GC_ERR_CUDA.  The colouring calls report the same failure
+ * as GC_ERR_TIMEOUT after a 10 s wait.
+ */
+int gc_debug_barrier_timeout(int device, int32_t timeout_ms, int32_t *error_word_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgc.so")
 SOURCES = ["gc_kernels.cu", "gc_api.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu", "gc_classes.cu", "gc_d2.cu",
-           "gc_host.cpp"]
+           "gc_diag.cu", "gc_host.cpp"]
 HEADERS = [os.path.join(CSRC, "gc_internal.h"), os.path.join(CSRC, "gc_device.cuh"), os.path.join(CSRC, "gc_ctx.h"),
            os.path.join(INCLUDE, "gc.h")]
 

@@ -84,9 +84,9 @@ __device__ __forceinline__ void st_color(int32_t *p, int v)
 // ------------------------------------------------------------------------
 
 // All nblocks blocks must be co-resident (cooperative launch).  A block that
-// waits longer than kBarrierTimeoutNs sets GC_EW_TIMEOUT and leaves; the
+// waits longer than timeout_ns (default 10 s) sets GC_EW_TIMEOUT and leaves; the
 // caller checks the error word after every barrier.
-static __device__ void grid_sync(DevState *st, unsigned nblocks)
+static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long long timeout_ns = kBarrierTimeoutNs)
 {
     PT_BEGIN(t_bar);
     __syncthreads();
@@ -104,7 +104,7 @@ static __device__ void grid_sync(DevState *st, unsigned nblocks)
                 unsigned polls = 0;
                 while (ld_acquire_u32(&st->bar_gen) == gen) {
                     __nanosleep(64);
-                    if (++polls > kBarrierMaxPolls || global_timer() - t0 > kBarrierTimeoutNs) {
+                    if (++polls > kBarrierMaxPolls || global_timer() - t0 > timeout_ns) {
                         atomicOr(&st->error, GC_EW_TIMEOUT);
                         break;
                     }

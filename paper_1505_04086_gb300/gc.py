@@ -137,6 +137,7 @@ _SIGS = {
     "gc_host_color": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                      ctypes.c_int32, _P, ctypes.POINTER(gc_stats)]),
     "gc_host_threads": (ctypes.c_int, []),
+    "gc_debug_barrier_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
 }
 
 _lock = threading.Lock()
@@ -420,6 +421,14 @@ def gc_host_color(row_ptr, col_idx, mode: int = 0, num_threads: int = 0, round_c
     rc = load().gc_host_color(ctypes.byref(csr), int(n), int(ci.size), int(mode), int(num_threads),
                               col.ctypes.data, ctypes.byref(st))
     return int(rc), col[:n], stats_dict(st, rs, rn)
+
+
+def gc_debug_barrier_timeout(device: int = 0, timeout_ms: int = 200):
+    """Run the bounded grid barrier against an arrival that never comes;
+    returns (status, device error word)."""
+    w = ctypes.c_int32(0)
+    rc = load().gc_debug_barrier_timeout(int(device), int(timeout_ms), ctypes.byref(w))
+    return int(rc), int(w.value)
 
 
 def gc_host_threads() -> int:
