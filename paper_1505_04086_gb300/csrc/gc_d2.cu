@@ -14,7 +14,10 @@
 // serialise one lane.  The colours of D2(v) are marked in a 2048-colour
 // shared-memory window per warp, the conflict test is taken in the same
 // scan, and First-Fit is the first clear bit (the window moves on and D2(v)
-// is read again only when 2048 colours are all taken).
+// is read again only when 2048 colours are all taken).  A vertex whose
+// two-hop neighbourhood has more than d2_heavy entries is flagged in the
+// prologue and inspected by a whole block (32768-colour window) after the
+// warps' share of each pass.
 //
 // GC_SCHED_DET: round 0 colours every vertex 1; iteration i reads the
 // colours of the end of iteration i-1 from one buffer and writes every
