@@ -164,8 +164,12 @@ typedef struct {
                                     (re)colouring, the tie side for a clean
                                     detection; 4 (index only) for a neighbour
                                     the asynchronous round 0 knows to be
-                                    uncoloured (in a tile not yet claimed); 4
-                                    per colour written and per worklist push;
+                                    uncoloured (in a tile not yet claimed);
+                                    in the first asynchronous repair of one
+                                    graph, a thread-path vertex reads 8 for
+                                    its round-0 mask and 8 per neighbour it
+                                    read as uncoloured there; 4 per colour
+                                    written and per worklist push;
                                     4 per vertex for a pass in which nothing
                                     is coloured yet.  GC_DIST2:
                                     per inspected vertex 4 (worklist entry,

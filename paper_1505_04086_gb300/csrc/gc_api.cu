@@ -80,6 +80,7 @@ int ensure_scratch(gc_ctx *c, int64_t n, bool need_b, bool batch, int64_t lut_en
     if (!c->wl0.reserve(vb) || !c->wl1.reserve(vb)) return GC_ERR_OOM;
     if (!c->hb0.reserve(vb) || !c->hb1.reserve(vb) || !c->hub_all.reserve(vb)) return GC_ERR_OOM;
     if (!c->mid_all.reserve(vb)) return GC_ERR_OOM;
+    if (!batch && !c->r0mask.reserve((size_t)std::max<int64_t>(n, 1) * sizeof(uint64_t))) return GC_ERR_OOM;
     if (batch && !c->lut.reserve((size_t)std::max<int64_t>(lut_entries, 1) * sizeof(int32_t))) return GC_ERR_OOM;
     if (!c->done.reserve(((size_t)std::max<int64_t>(n, 1) / 32 + 2) * sizeof(int32_t))) return GC_ERR_OOM;
     return GC_OK;
@@ -125,6 +126,11 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.tail = r.tail;
     p.window = r.window;
     p.d2_heavy = r.d2_heavy;
+    // Round-0 suspect masks: asynchronous RSOC on one graph whose first
+    // repair follows a round 0 over all of V with in-place repairs.
+    const bool masks = async && !batch && !(mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_FF_KEEPERS | GC_REPAIR_SNAPSHOT |
+                                                     GC_DIST2)) && p.touched == nullptr;
+    p.r0mask = masks ? c->r0mask.as<uint64_t>() : nullptr;
     p.done = c->done.as<int32_t>();
     p.gstat = c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();
@@ -358,7 +364,7 @@ void gc_ctx_destroy(gc_ctx *c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     if (c->ev_done) cudaEventSynchronize(c->ev_done);
-    for (Buf *b : {&c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
+    for (Buf *b : {&c->r0mask, &c->cB, &c->wl0, &c->wl1, &c->hb0, &c->hb1, &c->hub_all, &c->mid_all, &c->lut, &c->bitmap,
                    &c->round_sizes, &c->st, &c->done, &c->gstat, &c->uofs, &c->olist, &c->pitems, &c->cls, &c->stage_rp,
                    &c->stage_ci,
                    &c->stage_col})

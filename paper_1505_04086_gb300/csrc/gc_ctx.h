@@ -77,6 +77,7 @@ struct gc_ctx {
     gc::Buf cB, wl0, wl1, hb0, hb1, hub_all, mid_all, lut, bitmap, round_sizes, st, done, gstat, uofs, olist;
     gc::Buf pitems;                         // round-0 warp groups: one item per warp of the grid
     gc::Buf cls;                            // gc_color_classes: count matrix and scan sums
+    gc::Buf r0mask;                         // round-0 suspect masks (one graph, asynchronous RSOC)
     int32_t pitems_cap = 0;
     gc::Buf stage_rp, stage_ci, stage_col;  // gc_color host staging
     gc::DevState *st_host = nullptr;        // pinned

@@ -154,6 +154,8 @@ struct KParams {
     int64_t *pitems;           // round 0: (graph, warp, group size) of each grouped warp
     int32_t pitems_cap;        // its capacity (>= the grid's warps)
     int32_t d2_heavy;          // distance 2: two-hop entries above which a block inspects a vertex
+    uint64_t *r0mask;          // asynchronous round 0 of one graph: per suspect, the row positions of the
+                               // tie-side neighbours read as uncoloured (null: not kept)
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

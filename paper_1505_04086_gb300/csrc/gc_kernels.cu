@@ -313,7 +313,25 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
     }
     const int cv = ld_color<ASYNC>(R + v);
     mb += 4;
-    const bool d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t) || cv == 0;
+    bool d;
+    if (ASYNC && op == OP_RSOC && it == 1 && p.r0mask && !implicit) {
+        // First repair after round 0: only the neighbours this vertex read
+        // as uncoloured there can share its colour (see chunk_tent_ordered).
+        unsigned long long m = __ldcg(reinterpret_cast<const unsigned long long *>(p.r0mask) + v);
+        const auto row = ent.row(beg);
+        bool def = cv == 0;
+        t = 0;
+        while (m) {
+            const int i = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            ++t;
+            def |= ld_color<ASYNC>(R + nbase + row[i]) == cv;
+        }
+        d = def;
+        mb += 8;  // the mask
+    } else {
+        d = detect_thread<ASYNC>(ent, p.tie, v, beg, end, nbase, R, cv, op == OP_RSOC, t) || cv == 0;
+    }
     if (op == OP_DETECT) {
         if (!ASYNC) st_color<false>(p.cA + v, cv);  // two-phase: bring buffer A up to date
         mb += 8ll * t + (d ? 4 : 0);
@@ -779,6 +797,10 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // other as uncoloured: that endpoint is the suspect when the tie-break
     // makes it the one to recolour.
     bool suspect = mid;
+    // Row positions of the neighbours on the tie side read as uncoloured:
+    // the only ones that can clash with this lane after round 0 (the others
+    // were read with their final round-0 colours, which First-Fit avoided).
+    unsigned long long zmask = 0;
     // GC_FF_KEEPERS: only lower neighbours count, and the sorted row is read
     // up to v.
     // With degree tiers the higher neighbours read here may be final
@@ -841,7 +863,10 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
             for (int q = 0; q < kUnroll; ++q) {
                 const unsigned b = (unsigned)(c[q] - 1);
                 if (b < 64u) ext |= 1ull << b;
-                if (outside[q] && c[q] == 0 && on_tie_side(tie, u[q], v)) suspect = true;
+                if (outside[q] && c[q] == 0 && on_tie_side(tie, u[q], v)) {
+                    suspect = true;
+                    zmask |= 1ull << (i + q);  // i + q < deg <= t1 <= 62
+                }
             }
             if (keep && u[kUnroll - 1] < 0) break;  // row ended, or passed v
         }
@@ -854,6 +879,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     if (thr) {
         st_color<true>(C + v, mine);
         mb += 8 + 8ll * nread - 4ll * nskip + 4;  // index only for the unread colours
+        if (zmask && p.r0mask) __stcg(reinterpret_cast<unsigned long long *>(p.r0mask) + v, zmask);
     }
     __syncwarp();
     PT_BEGIN(t_mid);
