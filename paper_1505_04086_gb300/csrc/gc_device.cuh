@@ -154,6 +154,7 @@ static __device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, u
         if (low & 0xffffffffull) atomicOr(&bitmap[0], (uint32_t)low);
         if (low >> 32) atomicOr(&bitmap[1], (uint32_t)(low >> 32));
     }
+    __threadfence();  // this thread's updates land before the block reports done
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -163,11 +164,14 @@ static __device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, u
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // Every set bit is a colour <= the largest colour: only the words up to
+    // it are read (and cleared).
+    const int top = ld_volatile(&st->max_color);
+    const int words4 = min(kStatBitmapWords, (top >> 5) + 1 + 3) / 4;
     int s = 0;
     uint4 *bm4 = reinterpret_cast<uint4 *>(bitmap);
-    constexpr int kWords4 = kStatBitmapWords / 4;
 #pragma unroll 8
-    for (int w = threadIdx.x; w < kWords4; w += blockDim.x) {  // independent 16-byte loads in flight
+    for (int w = threadIdx.x; w < words4; w += blockDim.x) {  // independent 16-byte loads in flight
         uint4 x = __ldcg(bm4 + w);
         if (x.x | x.y | x.z | x.w) bm4[w] = make_uint4(0u, 0u, 0u, 0u);
         if (w == 0) x.x &= ~1u;  // colour 0 is not a colour
