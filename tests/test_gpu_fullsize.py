@@ -1,0 +1,120 @@
+"""Parity at the benchmark's full sizes, in the launch configurations the
+benchmark times (the library defaults and autotuned-style options: tile 32,
+2 blocks per SM): Kuhn 128^3 (2,097,152 vertices), R-MAT 2^22 (4,194,304
+vertices), the 4096-graph batch (186 M vertices) and distance 2 on Kuhn
+128^3.  Deterministic runs are compared with the oracle's replay bit for
+bit; asynchronous runs through validity (and the colour bound where the
+method meets it), and the batch on sampled graphs the oracle colours one by
+one."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1505_04086_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from paper_1505_04086_gb300 import gc  # noqa: E402
+
+OPTS = {"defaults": None, "tuned": {"t1": 62, "t2": 1024, "tile": 32, "blocks_per_sm": 2, "tail": 256}}
+DET, ASYNC = gc.GC_SCHED_DET, gc.GC_SCHED_ASYNC
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return I.workload("kuhn3d_128")
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return I.workload("rmat22_ef16")
+
+
+def run(ctx, g, mode, opts=None):
+    d = torch.device("cuda:0")
+    rp = torch.from_numpy(g.row_ptr).to(d)
+    ci = torch.from_numpy(g.col_idx).to(d)
+    col = torch.empty(g.n, dtype=torch.int32, device=d)
+    rc = gc.gc_color_async(ctx.handle, rp, ci, g.n, g.nnz, mode, col, opts)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    rc, st = gc.gc_ctx_stats(ctx.handle, 4096)
+    return rc, col.cpu().numpy(), st
+
+
+def assert_replay(col, st, ref):
+    assert np.array_equal(col, ref.colors), f"first diff at {np.nonzero(col != ref.colors)[0][:5]}"
+    assert (st["rounds"], st["conflicts"], st["model_bytes"]) == (ref.iterations, ref.conflicts, ref.model_bytes)
+    assert np.array_equal(st["round_sizes"], ref.round_sizes[: len(st["round_sizes"])])
+    assert (st["colors"], st["distinct_colors"]) == (ref.num_colors, ref.distinct_colors)
+
+
+@pytest.mark.parametrize("opts", list(OPTS))
+def test_kuhn128_det_equals_the_replay(ctx, c1, opts):
+    rc, col, st = run(ctx, c1, DET, OPTS[opts])
+    assert rc == gc.GC_OK
+    assert_replay(col, st, O.rsoc_det(c1))
+
+
+@pytest.mark.parametrize("opts", list(OPTS))
+def test_kuhn128_async_valid_within_bound(ctx, c1, opts):
+    rc, col, st = run(ctx, c1, ASYNC | gc.GC_CHECKED, OPTS[opts])
+    assert rc == gc.GC_OK
+    bad, mx, dist = O.check(c1, col)
+    assert bad == 0
+    assert mx <= 1.1 * int(O.ff(c1).max())
+    assert (st["colors"], st["distinct_colors"]) == (mx, dist)
+
+
+def test_rmat22_det_equals_the_replay(ctx, c2):
+    rc, col, st = run(ctx, c2, DET)
+    assert rc == gc.GC_OK
+    assert_replay(col, st, O.rsoc_det(c2))
+
+
+def test_rmat22_async_valid_and_tiers_within_bound(ctx, c2):
+    ff = int(O.ff(c2).max())
+    rc, col, st = run(ctx, c2, ASYNC | gc.GC_CHECKED)
+    assert rc == gc.GC_OK
+    bad, mx, _ = O.check(c2, col)
+    assert bad == 0 and st["colors"] == mx
+    rc, col, st = run(ctx, c2, ASYNC | gc.GC_TIERS | gc.GC_CHECKED)
+    assert rc == gc.GC_OK
+    bad, mx, _ = O.check(c2, col)
+    assert bad == 0
+    assert mx <= 1.1 * ff, (mx, ff)
+
+
+def test_kuhn128_distance2_async_valid(ctx, c1):
+    rc, col, st = run(ctx, c1, ASYNC | gc.GC_DIST2 | gc.GC_CHECKED)
+    assert rc == gc.GC_OK
+    assert O.check_d2(c1, col) == 0
+    assert st["colors"] == int(col.max())
+
+
+def test_batch4096_sampled_graphs_are_sequential_first_fit(ctx):
+    b = I.batch(4096, seed=I.SEED_BATCH)
+    d = "cuda:0"
+    vo, eo = torch.from_numpy(b.vtx_off).to(d), torch.from_numpy(b.edge_off).to(d)
+    rp, ci = torch.from_numpy(b.row_ptr).to(d), torch.from_numpy(b.col_idx).to(d)
+    col, rounds, confl, rc, st = ctx.color_batch(vo, eo, rp, ci, b.total_n, b.total_nnz, mode=ASYNC | gc.GC_CHECKED,
+                                                 check=False)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    rounds, confl = rounds.cpu().numpy(), confl.cpu().numpy()
+    del vo, eo, rp, ci
+    rng = np.random.default_rng(1505)
+    sample = set(rng.choice(b.G, size=40, replace=False).tolist())
+    sizes = np.diff(b.vtx_off)
+    sample |= {int(np.argmax(sizes)), int(np.argmin(sizes))}  # the largest and smallest graphs too
+    for g in sorted(sample):
+        v0, v1 = int(b.vtx_off[g]), int(b.vtx_off[g + 1])
+        sub = b.graph(g)
+        assert np.array_equal(col[v0:v1].cpu().numpy(), O.ff(sub)), f"graph {g}"
+        assert rounds[g] == 1 and confl[g] == 0, f"graph {g}"
