@@ -468,11 +468,20 @@ def host_openmp(gc, g, runs=3):
 
     t, r, c, k = timed(MODES["rsoc_async"])
     t2, r2, c2, k2 = timed(MODES["twophase_async"])
-    return {"value": round(g.num_edges / (t / 1e3), 1), "unit": "edges/s", "threads": threads,
-            "ms": round(t, 3), "rounds": r, "conflicts": c, "colors": k, "runs": runs,
-            "kind": "gc_host_color (Algorithm 3, asynchronous, OpenMP dynamic schedule)",
-            "twophase": {"ms": round(t2, 3), "rounds": r2, "conflicts": c2, "colors": k2,
-                         "rsoc_speedup": round(t2 / t, 3)}}
+    out = {"value": round(g.num_edges / (t / 1e3), 1), "unit": "edges/s", "threads": threads,
+           "ms": round(t, 3), "rounds": r, "conflicts": c, "colors": k, "runs": runs,
+           "kind": "gc_host_color (Algorithm 3, asynchronous, OpenMP dynamic schedule)",
+           "twophase": {"ms": round(t2, 3), "rounds": r2, "conflicts": c2, "colors": k2,
+                        "rsoc_speedup": round(t2 / t, 3)}}
+    # distance 2 on the host too (one run), where the bench times it on the GPU
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    if int((deg * deg).sum()) <= 4_000_000_000:
+        rc, _, st = gc.gc_host_color(g.row_ptr, g.col_idx, MODES["rsoc_async"] | gc.GC_DIST2, threads)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
+        out["distance2"] = {"ms": round(st["elapsed_ms"], 3), "rounds": st["rounds"], "colors": st["colors"],
+                            "runs": 1}
+    return out
 
 
 def cpu_baseline(g, budget_s=12.0):

@@ -525,7 +525,9 @@ int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, c
  *         the same colouring, iterations, conflicts and round sizes as
  *         gc_color in GC_SCHED_DET, whatever the thread count), either
  *         tie-break, GC_CHECKED (verify the result on the host;
- *         GC_ERR_CHECK if invalid) and GC_NO_COLOR_STATS; any other bit gives
+ *         GC_ERR_CHECK if invalid), GC_NO_COLOR_STATS and GC_DIST2 (the same
+ *         algorithms over two-hop neighbourhoods: deterministic forms equal
+ *         the distance-2 replay of gc_color); any other bit gives
  *         GC_ERR_ARG.
  *   num_threads: OpenMP threads (0 = the OpenMP default).  With one thread
  *         GC_SCHED_ASYNC RSOC is sequential First-Fit in id order.

@@ -33,7 +33,8 @@
 
 namespace {
 
-constexpr uint32_t kHostModes = GC_ALG_TWO_PHASE | GC_SCHED_ASYNC | GC_TIE_HIGHER_KEEPS | GC_CHECKED | GC_NO_COLOR_STATS;
+constexpr uint32_t kHostModes =
+    GC_ALG_TWO_PHASE | GC_SCHED_ASYNC | GC_TIE_HIGHER_KEEPS | GC_CHECKED | GC_NO_COLOR_STATS | GC_DIST2;
 
 inline int32_t ld(const int32_t *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
 inline void st(int32_t *p, int32_t v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
@@ -43,6 +44,7 @@ struct Graph {
     const int32_t *ci;
     int32_t n;
     bool higher_keeps;
+    bool dist2;  // neighbourhood = two-hop neighbourhood D2(v) (GC_DIST2)
     // whether a clash of v with u is v's to repair
     bool tie_side(int32_t u, int32_t v) const { return higher_keeps ? u > v : u < v; }
 };
@@ -53,26 +55,41 @@ struct Marks {
     int64_t cur = 0;
 };
 
-// Smallest colour >= 1 held by no neighbour of v in col.
+// Smallest colour >= 1 held by no neighbour of v in col (with dist2: by no
+// vertex of D2(v), the neighbours u of v and every w != v adjacent to one).
 int32_t first_fit(const Graph &g, int32_t v, const int32_t *col, Marks &m)
 {
-    const int32_t deg = g.rp[v + 1] - g.rp[v];
+    const int64_t top = (int64_t)m.stamp.size() - 1;  // a free colour lies in 1..top
     ++m.cur;
     for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) {
-        const int32_t c = ld(col + g.ci[k]);
-        if (c >= 1 && c <= deg + 1) m.stamp[c] = m.cur;
+        const int32_t u = g.ci[k];
+        const int32_t c = ld(col + u);
+        if (c >= 1 && c <= top) m.stamp[c] = m.cur;
+        if (!g.dist2) continue;
+        for (int32_t j = g.rp[u]; j < g.rp[u + 1]; ++j) {
+            const int32_t w = g.ci[j];
+            if (w == v) continue;
+            const int32_t cw = ld(col + w);
+            if (cw >= 1 && cw <= top) m.stamp[cw] = m.cur;
+        }
     }
     int32_t k = 1;
     while (m.stamp[k] == m.cur) ++k;
     return k;
 }
 
-// Whether a neighbour of v on its tie side holds colour cv in col.
+// Whether a neighbour (dist2: a vertex of D2(v)) of v on its tie side holds
+// colour cv in col.
 bool clashes(const Graph &g, int32_t v, int32_t cv, const int32_t *col)
 {
     for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) {
         const int32_t u = g.ci[k];
         if (g.tie_side(u, v) && ld(col + u) == cv) return true;
+        if (!g.dist2) continue;
+        for (int32_t j = g.rp[u]; j < g.rp[u + 1]; ++j) {
+            const int32_t w = g.ci[j];
+            if (w != v && g.tie_side(w, v) && ld(col + w) == cv) return true;
+        }
     }
     return false;
 }
@@ -117,13 +134,15 @@ struct Run {
     bool capped = false;
 };
 
-void color_host(const Graph &g, uint32_t mode, int T, int32_t *c, int32_t max_deg, Run &r)
+// top: the largest colour First-Fit can return (the largest neighbourhood
+// + 1).
+void color_host(const Graph &g, uint32_t mode, int T, int32_t *c, int64_t top, Run &r)
 {
     const int32_t n = g.n;
     const bool async = mode & GC_SCHED_ASYNC;
     const bool twop = mode & GC_ALG_TWO_PHASE;
     std::vector<Marks> marks(T);
-    for (auto &m : marks) m.stamp.assign((size_t)max_deg + 2, 0);
+    for (auto &m : marks) m.stamp.assign((size_t)top + 1, 0);
     std::vector<std::vector<int32_t>> local(T);
     std::vector<int32_t> U, L, fresh;  // fresh: deterministic forms, new colour per worklist entry
     std::vector<char> flag;
@@ -210,14 +229,25 @@ extern "C" int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX || num_threads < 0 || (mode & ~kHostModes)) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
-    const Graph g{csr->row_ptr, csr->col_idx, n, (mode & GC_TIE_HIGHER_KEEPS) != 0};
-    int32_t max_deg = 0;
-    for (int32_t v = 0; v < n; ++v) max_deg = std::max(max_deg, g.rp[v + 1] - g.rp[v]);
+    const Graph g{csr->row_ptr, csr->col_idx, n, (mode & GC_TIE_HIGHER_KEEPS) != 0, (mode & GC_DIST2) != 0};
+    // the largest neighbourhood: degree, or two-hop entries (sum of the
+    // neighbours' degrees) with GC_DIST2
+    int64_t widest = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        int64_t w = g.rp[v + 1] - g.rp[v];
+        if (g.dist2) {
+            w = 0;
+            for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) w += g.rp[g.ci[k] + 1] - g.rp[g.ci[k]];
+        }
+        widest = std::max(widest, w);
+    }
+    if (widest > INT32_MAX - 2) return GC_ERR_ARG;
     const int T = threads_for(num_threads);
     Run r;
     const auto t0 = std::chrono::steady_clock::now();
     try {
-        if (n > 0) color_host(g, mode, T, colors_out, max_deg, r);
+        // colours never exceed the neighbourhood size + 1, nor n
+        if (n > 0) color_host(g, mode, T, colors_out, std::min<int64_t>(widest, n) + 1, r);
     } catch (const std::bad_alloc &) {
         return GC_ERR_OOM;
     }
@@ -226,9 +256,14 @@ extern "C" int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t
     if (status == GC_OK && (mode & GC_CHECKED)) {
         for (int32_t v = 0; v < n && status == GC_OK; ++v) {
             const int32_t cv = colors_out[v];
-            if (cv < 1 || cv > g.rp[v + 1] - g.rp[v] + 1) status = GC_ERR_CHECK;
-            for (int32_t k = g.rp[v]; k < g.rp[v + 1] && status == GC_OK; ++k)
-                if (colors_out[g.ci[k]] == cv) status = GC_ERR_CHECK;
+            if (cv < 1 || (!g.dist2 && cv > g.rp[v + 1] - g.rp[v] + 1)) status = GC_ERR_CHECK;
+            for (int32_t k = g.rp[v]; k < g.rp[v + 1] && status == GC_OK; ++k) {
+                const int32_t u = g.ci[k];
+                if (colors_out[u] == cv) status = GC_ERR_CHECK;
+                if (g.dist2)
+                    for (int32_t j = g.rp[u]; j < g.rp[u + 1] && status == GC_OK; ++j)
+                        if (g.ci[j] != v && colors_out[g.ci[j]] == cv) status = GC_ERR_CHECK;
+            }
         }
     }
     if (stats_out) {

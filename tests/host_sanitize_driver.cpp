@@ -1,6 +1,7 @@
 // Host AddressSanitizer / UndefinedBehaviorSanitizer run of the paper's
-// OpenMP form (gc_host_color): every mode on generated graphs, several
-// thread counts, the library's own check of each result (GC_CHECKED).
+// OpenMP form (gc_host_color): every mode on generated graphs (distance 2
+// too, on the small meshes), several thread counts, the library's own check
+// of each result (GC_CHECKED).
 #include <cstdio>
 #include <cstdint>
 #include <initializer_list>
@@ -36,17 +37,20 @@ int main()
         gc_csr csr{gcgen_row_ptr(g), gcgen_col_idx(g)};
         int32_t *col = new int32_t[n > 0 ? n : 1];
         int32_t rs[256];
+        const bool small = n <= 1100;  // distance 2 on the small meshes only
         for (uint32_t m : modes)
-            for (int t : {1, 3, 8}) {
-                gc_stats st{};
-                st.round_sizes = rs;
-                st.round_sizes_cap = 256;
-                const int rc = gc_host_color(&csr, n, gcgen_nnz(g), m | GC_CHECKED, t, col, &st);
-                if (rc != GC_OK) {
-                    std::fprintf(stderr, "FAILED: mode %u threads %d status %d\n", m, t, rc);
-                    ++failures;
+            for (uint32_t d2 : {0u, (uint32_t)GC_DIST2})
+                for (int t : {1, 3, 8}) {
+                    if (d2 && !small) continue;
+                    gc_stats st{};
+                    st.round_sizes = rs;
+                    st.round_sizes_cap = 256;
+                    const int rc = gc_host_color(&csr, n, gcgen_nnz(g), m | d2 | GC_CHECKED, t, col, &st);
+                    if (rc != GC_OK) {
+                        std::fprintf(stderr, "FAILED: mode %u threads %d status %d\n", m | d2, t, rc);
+                        ++failures;
+                    }
                 }
-            }
         delete[] col;
         gcgen_free(g);
     }

@@ -70,9 +70,40 @@ def test_host_async_is_a_proper_colouring(g, alg, tie):
 def test_host_mode_bits_are_checked():
     g = I.kuhn3d(3)
     for bad in (gc.GC_VALIDATE, gc.GC_DEBUG_NO_TIEBREAK, gc.GC_REPAIR_SNAPSHOT, gc.GC_TIERS, gc.GC_FF_KEEPERS,
-                gc.GC_DIST2, 1 << 20):
+                1 << 20):
         rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, ASYNC | bad, 2)
         assert rc == gc.GC_ERR_ARG, bad
     rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, 0, -1)
     assert rc == gc.GC_ERR_ARG
     assert gc.gc_host_threads() >= 1
+
+
+D2_GRAPHS = [I.from_edges(7, [(i, i + 1) for i in range(6)]), I.from_edges(40, [(0, i) for i in range(1, 40)]),
+             I.kuhn3d(8), I.tri2d(30, 30, 0.3), I.rmat(9)]
+D2_IDS = [f"{g.name}-{g.n}" for g in D2_GRAPHS]
+
+
+@pytest.mark.parametrize("g", D2_GRAPHS, ids=D2_IDS)
+@pytest.mark.parametrize("alg", [0, TWOP], ids=["rsoc", "twophase"])
+@pytest.mark.parametrize("tie", [0, HIGHER], ids=["lower", "higher"])
+@pytest.mark.parametrize("threads", [1, 8])
+def test_host_distance2_det_matches_the_oracle_replay(g, alg, tie, threads):
+    # both algorithms over two-hop neighbourhoods give the distance-2 replay
+    # (the snapshot equivalence of Algorithms 2 and 3 holds on G^2 as well)
+    rc, col, st = gc.gc_host_color(g.row_ptr, g.col_idx, gc.GC_DIST2 | alg | tie | gc.GC_CHECKED, threads,
+                                   round_cap=4096)
+    ref = O.rsoc_det_d2(g, O.TIE_HIGHER_KEEPS if tie else O.TIE_LOWER_KEEPS)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    assert np.array_equal(col, ref.colors)
+    assert (st["rounds"], st["conflicts"]) == (ref.iterations, ref.conflicts)
+    assert np.array_equal(st["round_sizes"], ref.round_sizes)
+
+
+@pytest.mark.parametrize("g", D2_GRAPHS, ids=D2_IDS)
+def test_host_distance2_async(g):
+    rc, col, _ = gc.gc_host_color(g.row_ptr, g.col_idx, gc.GC_DIST2 | ASYNC, 1)
+    assert rc == gc.GC_OK
+    assert np.array_equal(col, O.ff_d2(g))  # one thread: sequential First-Fit over D2
+    rc, col, _ = gc.gc_host_color(g.row_ptr, g.col_idx, gc.GC_DIST2 | ASYNC | gc.GC_CHECKED, 8)
+    assert rc == gc.GC_OK
+    assert O.check_d2(g, col) == 0
