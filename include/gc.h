@@ -112,7 +112,8 @@ enum {
                                     "neighbour" read as "vertex of D2(v)" (the
                                     neighbours u of v and every w != v adjacent
                                     to such a u).  Single graph only
-                                    (gc_color, gc_color_async; GC_ERR_ARG in
+                                    (gc_color, gc_color_async, and the host
+                                    form gc_host_color; GC_ERR_ARG in
                                     the batch, plan, server, no-alloc,
                                     recolour and autotune calls) and only with
                                     GC_ALG_RSOC, either schedule, either
