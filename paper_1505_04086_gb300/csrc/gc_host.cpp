@@ -82,6 +82,17 @@ int32_t first_fit(const Graph &g, int32_t v, const int32_t *col, Marks &m)
 // colour cv in col.
 bool clashes(const Graph &g, int32_t v, int32_t cv, const int32_t *col)
 {
+    if (!g.dist2) {
+        // rows are sorted: the tie side is a prefix (lower ids) or a suffix
+        if (!g.higher_keeps) {
+            for (int32_t k = g.rp[v]; k < g.rp[v + 1] && g.ci[k] < v; ++k)
+                if (ld(col + g.ci[k]) == cv) return true;
+        } else {
+            for (int32_t k = g.rp[v + 1] - 1; k >= g.rp[v] && g.ci[k] > v; --k)
+                if (ld(col + g.ci[k]) == cv) return true;
+        }
+        return false;
+    }
     for (int32_t k = g.rp[v]; k < g.rp[v + 1]; ++k) {
         const int32_t u = g.ci[k];
         if (g.tie_side(u, v) && ld(col + u) == cv) return true;
