@@ -136,8 +136,9 @@ static gcgen_csr *csr_from_pairs(int32_t n, int64_t m, const int32_t *eu, const 
     free(rp);
     g->n = n;
     g->nnz = w;
-    g->col_idx = (int32_t *)realloc(col, (size_t)(w > 0 ? w : 1) * sizeof(int32_t));
-    if (!g->col_idx) g->col_idx = col;
+    /* shrink to the deduplicated size; on failure keep the larger block */
+    int32_t *shrunk = (int32_t *)realloc(col, (size_t)(w > 0 ? w : 1) * sizeof(int32_t));
+    g->col_idx = shrunk ? shrunk : col;
     free(cnt);
     return g;
 fail:
