@@ -1,8 +1,10 @@
 """ctypes binding of libgc (include/gc.h): argument marshalling only.
 
-Every step of the colouring runs in the CUDA library; this module converts
-torch tensors / numpy arrays to pointers and structs and back.  It raises if
-libgc.so has not been built: there is no CPU fallback.
+Every step of the colouring runs in the library (CUDA kernels; the paper's
+OpenMP form, gc_host_color, is the library's separate host entry point);
+this module converts torch tensors / numpy arrays to pointers and structs
+and back.  It raises if libgc.so has not been built: there is no CPU
+fallback.
 
 The entry points keep the C names (gc_color, gc_color_async, gc_ctx_stats,
 gc_color_batch, ...); :class:`Context` is a small convenience wrapper.
