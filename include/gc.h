@@ -226,6 +226,19 @@ typedef struct {
                                     neighbours' degrees) than this is inspected
                                     by a whole block, the others by one warp;
                                     0 = 4096 */
+    int32_t core_deg;            /* GC_SCHED_ASYNC on one graph (gc_color,
+                                    gc_color_async, gc_color_noalloc; not
+                                    with GC_TIERS, GC_FF_KEEPERS or GC_DIST2):
+                                    the vertices of degree above max(core_deg,
+                                    t2) -- if there are at most 4096 of them --
+                                    form the core, coloured before round 0 one
+                                    at a time in decreasing degree (ties:
+                                    increasing id) by First-Fit among
+                                    themselves; they keep those colours, so
+                                    the repair rounds never rescan their rows
+                                    and a dense core of hubs (R-MAT) does not
+                                    drive the colour count up.  0 = 4096,
+                                    -1 = no core */
 } gc_opts;
 
 typedef struct gc_ctx gc_ctx;
@@ -485,11 +498,15 @@ void gc_server_destroy(gc_server *s);
  * that must not allocate memory while they run: code whose device memory is
  * owned by another allocator under a hard budget, or latency-critical loops
  * that cannot afford a cudaMalloc/cudaFree (either may synchronise the
- * device).  Same colouring as gc_color_async + gc_ctx_stats (every mode bit
- * and gc_opts field behaves the same), but no context is needed and nothing
- * is allocated: all working memory comes from one fixed array of about 7 MB
- * compiled into the library, which every GPU that loads the library holds
- * until the process exits.
+ * device).  Colours one graph as gc_color_async + gc_ctx_stats do, but no
+ * context is needed and nothing is allocated: all working memory comes from
+ * one fixed array of about 7 MB compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  Differences from
+ * gc_color_async: GC_DIST2 is rejected (GC_ERR_ARG) and d2_heavy is
+ * ignored; asynchronous RSOC keeps no round-0 suspect masks, so its first
+ * repair reads whole tie sides and its work counters (model_bytes) can
+ * differ from the allocating call's.  Deterministic modes give exactly the
+ * allocating call's colouring and statistics.
  *
  *   csr, colors_out: DEVICE pointers (host pointers give GC_ERR_ARG: staging
  *                    them would need memory); the caller owns them.
@@ -525,7 +542,9 @@ int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, c
  *         iteration sees the colours of the end of the iteration before:
  *         the same colouring, iterations, conflicts and round sizes as
  *         gc_color in GC_SCHED_DET, whatever the thread count), either
- *         tie-break, GC_CHECKED (verify the result on the host;
+ *         tie-break, GC_VALIDATE (check the CSR on the host first, as
+ *         gc_color does on the device: GC_ERR_GRAPH if malformed),
+ *         GC_CHECKED (verify the result on the host;
  *         GC_ERR_CHECK if invalid), GC_NO_COLOR_STATS and GC_DIST2 (the same
  *         algorithms over two-hop neighbourhoods: deterministic forms equal
  *         the distance-2 replay of gc_color); any other bit gives
@@ -535,9 +554,11 @@ int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, c
  *   stats_out (may be NULL): rounds, conflicts, colors, distinct_colors,
  *         round_sizes (as for gc_ctx_stats), elapsed_ms = host wall time of
  *         the colouring; model_bytes and error_word are 0.
- * Returns GC_OK, GC_ERR_ARG, GC_ERR_OOM, GC_ERR_NO_CONVERGENCE (n+1
- * iterations with conflicts left; colors_out holds the colouring at the cap)
- * or GC_ERR_CHECK.  A malformed graph is not detected (keep indices in range).
+ * Returns GC_OK, GC_ERR_ARG, GC_ERR_OOM, GC_ERR_GRAPH, GC_ERR_NO_CONVERGENCE
+ * (n+1 iterations with conflicts left; colors_out holds the colouring at the
+ * cap) or GC_ERR_CHECK.  Without GC_VALIDATE a malformed graph is not
+ * detected: unsorted rows give an invalid colouring and out-of-range
+ * indices are read out of bounds.
  */
 int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t num_threads,
                   int32_t *colors_out, gc_stats *stats_out);

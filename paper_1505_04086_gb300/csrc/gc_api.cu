@@ -40,7 +40,7 @@ bool is_device_ptr(const void *p)
 }
 
 struct Resolved {
-    int32_t max_rounds, t1, t2, tile, tail, blocks_per_sm, window, d2_heavy;
+    int32_t max_rounds, t1, t2, tile, tail, blocks_per_sm, window, d2_heavy, core_deg;
 };
 
 int resolve_opts(const gc_opts *o, int64_t n, uint32_t mode, Resolved &r)
@@ -58,6 +58,8 @@ int resolve_opts(const gc_opts *o, int64_t n, uint32_t mode, Resolved &r)
     if (r.window < -1) return GC_ERR_ARG;
     if (o->d2_heavy < 0) return GC_ERR_ARG;
     r.d2_heavy = o->d2_heavy > 0 ? o->d2_heavy : 4096;
+    if (o->core_deg < -1) return GC_ERR_ARG;
+    r.core_deg = o->core_deg > 0 ? o->core_deg : (o->core_deg < 0 ? 0 : gc::kCoreDeg);
     if (r.t1 > gc::kT1Max || r.t2 > gc::kT2Max || r.t1 > r.t2) return GC_ERR_ARG;
     if (r.tile % 32 != 0 || r.tile > 4096) return GC_ERR_ARG;
     if (r.blocks_per_sm < 0) return GC_ERR_ARG;
@@ -131,6 +133,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     const bool masks = async && !batch && !(mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_FF_KEEPERS | GC_REPAIR_SNAPSHOT |
                                                      GC_DIST2)) && p.touched == nullptr;
     p.r0mask = masks ? c->r0mask.as<uint64_t>() : nullptr;
+    p.core_deg = gc::core_applies(mode, batch, p.touched != nullptr) ? r.core_deg : 0;
     p.done = c->done.as<int32_t>();
     p.gstat = c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();

@@ -33,8 +33,32 @@
 
 namespace {
 
-constexpr uint32_t kHostModes =
-    GC_ALG_TWO_PHASE | GC_SCHED_ASYNC | GC_TIE_HIGHER_KEEPS | GC_CHECKED | GC_NO_COLOR_STATS | GC_DIST2;
+constexpr uint32_t kHostModes = GC_ALG_TWO_PHASE | GC_SCHED_ASYNC | GC_TIE_HIGHER_KEEPS | GC_VALIDATE | GC_CHECKED |
+                                GC_NO_COLOR_STATS | GC_DIST2;
+
+// GC_VALIDATE: the input format every loop relies on -- row pointers from 0
+// to nnz without decreasing, indices in 0..n-1, rows strictly ascending
+// (the tie-side scans read a prefix or suffix), no self-loops, and every
+// entry (v,u) mirrored by (u,v).  Reads row pointers before the entries
+// they bound, so malformed input is never read out of bounds.
+bool valid_csr(const int32_t *rp, const int32_t *ci, int32_t n, int64_t nnz)
+{
+    if (rp[0] != 0 || rp[n] != nnz) return false;
+    for (int32_t v = 0; v < n; ++v)
+        if (rp[v + 1] < rp[v]) return false;
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = rp[v]; k < rp[v + 1]; ++k) {
+            const int32_t u = ci[k];
+            if (u < 0 || u >= n || u == v) return false;
+            if (k > rp[v] && ci[k - 1] >= u) return false;
+        }
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t k = rp[v]; k < rp[v + 1]; ++k) {
+            const int32_t u = ci[k];
+            if (!std::binary_search(ci + rp[u], ci + rp[u + 1], v)) return false;
+        }
+    return true;
+}
 
 inline int32_t ld(const int32_t *p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
 inline void st(int32_t *p, int32_t v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
@@ -240,6 +264,7 @@ extern "C" int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX || num_threads < 0 || (mode & ~kHostModes)) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
+    if ((mode & GC_VALIDATE) && n > 0 && !valid_csr(csr->row_ptr, csr->col_idx, n, nnz)) return GC_ERR_GRAPH;
     const Graph g{csr->row_ptr, csr->col_idx, n, (mode & GC_TIE_HIGHER_KEEPS) != 0, (mode & GC_DIST2) != 0};
     // the largest neighbourhood: degree, or two-hop entries (sum of the
     // neighbours' degrees) with GC_DIST2

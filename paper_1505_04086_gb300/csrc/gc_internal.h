@@ -34,6 +34,9 @@ constexpr int kOrderedGroup = 1 << 18;  // graphs this small without hubs or wid
 constexpr int kPipeMaxK = 512;          // largest warp group colouring one graph in id order
 constexpr int kPipeMinChunks = 8;       // fewest chunks per warp of a group
 constexpr int kTargetSteps = 32;        // candidate chunk shares per grouped warp (x1.1 apart)
+constexpr int kCoreDeg = 4096;          // asynchronous single graph: default degree above which a vertex is in the core
+constexpr int kCoreMax = 4096;          // largest core coloured one vertex at a time before round 0
+constexpr int kCoreSeg = 1024;          // adjacency entries per task of the core's adjacency build
 
 enum Op : int { OP_TENT = 0, OP_RSOC = 1, OP_DETECT = 2 };
 
@@ -56,6 +59,14 @@ inline bool mode_ok(uint32_t mode)
 // Mode bits of the calls that colour with the distance-1 kernel only
 // (batches, plans, the server, the no-alloc and recolour calls, autotuning).
 inline bool dist1_mode_ok(uint32_t mode) { return mode_ok(mode) && !(mode & GC_DIST2); }
+
+// Whether a colouring in this mode colours the core of high-degree vertices
+// first (asynchronous, one graph, a full colouring, the plain First-Fit
+// choices of Algorithm 2 or 3 and one stage for all degrees).
+inline bool core_applies(uint32_t mode, bool batch, bool recolor)
+{
+    return (mode & GC_SCHED_ASYNC) && !batch && !recolor && !(mode & (GC_TIERS | GC_FF_KEEPERS | GC_DIST2));
+}
 
 // The second n-entry buffer holds colours (deterministic mode, snapshot
 // repairs) or, with GC_FF_KEEPERS, the round a vertex was last queued for.
@@ -108,6 +119,10 @@ struct DevState {
     int d2_hcount[kRing];            // distance-2: heavy vertices pushed per iteration
     int d2_hclaim[kRing];            // distance-2: heavy vertices claimed per iteration
     int d2_hclaim0;                  // distance-2: heavy vertices claimed in round 0
+    int core_count;                  // vertices of degree > core_deg found by the prologue
+    int core_n;                      // of which coloured as the core before round 0 (0: no core)
+    int core_task;                   // core adjacency build: next task
+    int core_colors;                 // largest colour of the core
 };
 
 struct KParams {
@@ -156,6 +171,8 @@ struct KParams {
     int32_t d2_heavy;          // distance 2: two-hop entries above which a block inspects a vertex
     uint64_t *r0mask;          // asynchronous round 0 of one graph: per suspect, the row positions of the
                                // tie-side neighbours read as uncoloured (null: not kept)
+    int32_t core_deg;          // asynchronous single graph: vertices of degree > core_deg (and > t2) are
+                               // coloured first, one at a time in decreasing degree (0: no core)
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

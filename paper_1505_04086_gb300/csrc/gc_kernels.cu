@@ -1533,7 +1533,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
     int *out_hub = p.hub[it & 1];
     const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS);
 
-    // hubs: one block per vertex, longest tasks first
+    // hubs: one block per vertex
     if (in.hn > 0) {
         int *claim = &st->pass_hub[q & (kRing - 1)];
         for (;;) {
@@ -1757,6 +1757,235 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
 }
 
 
+// ------------------------------------------------------------------------
+// the core: the highest-degree vertices of one graph, coloured first
+// ------------------------------------------------------------------------
+//
+// In the asynchronous mode a graph with very high-degree vertices (R-MAT's
+// hubs, which form a dense core) gets them coloured before round 0 of the
+// rest, one vertex at a time in decreasing degree (ties: increasing id), by
+// First-Fit among themselves: the interleaving of Algorithm 3's round 0 in
+// which the threads holding the core run first and one after the other.
+// They then hold final colours that no later round changes (every other
+// vertex avoids them), so the repair rounds never rescan a hub row, and the
+// colour count stays close to sequential First-Fit (the core decides it).
+//
+// Data: p.mid_all lists the core (rank order after core_sort); while the
+// core is built, a core vertex's colour slot holds -(rank + 1); p.wl[1]
+// holds the core's adjacency as a bit matrix, word w of rank r at
+// w * H + r (column-major: the 32 ranks of a batch are one coalesced read);
+// p.hub[1][r] is the first adjacency-build task of rank r (H + 1 entries).
+
+// Exclusive prefix sum over the block of one value per thread (all threads
+// call it); `scratch` holds kWarps ints of shared memory.
+__device__ __forceinline__ int block_exclusive_scan(int x, int *scratch, int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) scratch[wid] = incl;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        const int t = scratch[w];
+        if (w < wid) before += t;
+        total += t;
+    }
+    __syncthreads();
+    return before + incl - x;
+}
+
+// Block 0: sort the core by (degree descending, id ascending), write it back
+// in rank order, mark the colour slots and list the build tasks.
+__device__ __noinline__ void core_sort(const KParams &p, Shared &sh, int H)
+{
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(&sh.seg[0][0][0]);  // kCoreMax keys
+    static_assert(sizeof(sh.seg) >= kCoreMax * sizeof(unsigned long long), "core keys fit the staging area");
+    int P = 1;
+    while (P < H) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += kBlock) {
+        unsigned long long k = ~0ull;
+        if (i < H) {
+            const int32_t v = __ldcg(p.mid_all + i);
+            const int32_t d = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
+            k = ((unsigned long long)(~(uint32_t)d) << 32) | (uint32_t)v;
+        }
+        key[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)  // bitonic sort, ascending keys
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += kBlock) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long a = key[lo], b = key[hi];
+                if ((a > b) == up) {
+                    key[lo] = b;
+                    key[hi] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = threadIdx.x; r < H; r += kBlock) {
+        const int32_t v = (int32_t)(uint32_t)key[r];
+        __stcg(p.mid_all + r, v);
+        st_color<true>(p.cA + v, -(r + 1));
+    }
+    // tasks of kCoreSeg adjacency entries per rank, prefix-summed into p.hub[1]
+    constexpr int kPer = kCoreMax / kBlock;
+    int tasks[kPer];
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int r = threadIdx.x * kPer + q;
+        tasks[q] = 0;
+        if (r < H) {
+            const int d = (int)~(uint32_t)(key[r] >> 32);
+            tasks[q] = (d + kCoreSeg - 1) / kCoreSeg;
+        }
+        sum += tasks[q];
+    }
+    int total;
+    int before = block_exclusive_scan(sum, reinterpret_cast<int *>(sh.warp_bm), total);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int r = threadIdx.x * kPer + q;
+        if (r < H) __stcg(p.hub[1] + r, before);
+        before += tasks[q];
+    }
+    if (threadIdx.x == 0) __stcg(p.hub[1] + H, total);
+    __syncthreads();
+}
+
+// All blocks: the core's adjacency bit matrix, from the core vertices' rows
+// (a neighbour is in the core when its colour slot holds a rank mark).
+// Tasks of kCoreSeg entries are claimed warp by warp.
+__device__ __noinline__ void core_build(const KParams &p, int H, long long &mb)
+{
+    const int lane = threadIdx.x & 31;
+    const int32_t *tpfx = p.hub[1];
+    const int T = __ldcg(tpfx + H);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(p.wl[1]);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&p.st->core_task, 1);
+        t = __shfl_sync(FULL_MASK, t, 0);
+        if (t >= T) break;
+        int lo = 0, hi = H - 1;  // the rank whose tasks hold t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldcg(tpfx + mid) <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int r = lo;
+        const int k = t - __ldcg(tpfx + r);
+        const int32_t v = __ldcg(p.mid_all + r);
+        const int32_t rb = __ldg(p.row_ptr + v), re = __ldg(p.row_ptr + v + 1);
+        const int32_t beg = rb + k * kCoreSeg;
+        const int32_t end = min(re, beg + kCoreSeg);
+        for (int32_t i0 = beg; i0 < end; i0 += 32 * kUnroll) {
+            int32_t u[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) {
+                const int32_t i = i0 + q * 32 + lane;
+                u[q] = i < end ? __ldg(p.col_idx + i) : -1;
+            }
+            int c[kUnroll];
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q) c[q] = u[q] >= 0 ? __ldcg(p.cA + u[q]) : 0;
+#pragma unroll
+            for (int q = 0; q < kUnroll; ++q)
+                if (c[q] < 0) {
+                    const int j = -c[q] - 1;
+                    atomicOr(bits + (size_t)(j >> 5) * H + r, 1u << (j & 31));
+                }
+        }
+        // First-Fit of a core vertex reads its row (index + colour), its row
+        // pointers and writes its colour.
+        if (lane == 0) mb += 8ll * (end - beg) + (k == 0 ? 12 : 0);
+    }
+}
+
+// Block 0: sequential First-Fit over the core in rank order, 32 ranks at a
+// time: first every vertex of the batch collects the colours of its core
+// neighbours in earlier batches (all warps, bits of the matrix), then warp 0
+// resolves the batch in rank order (each vertex also avoids the colours just
+// given to its lower-ranked neighbours in the batch).  The colours go to
+// p.cA and, if not null, to `also` (the second buffer of snapshot repairs,
+// which only inspected vertices are written to).  Returns the largest colour.
+__device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int32_t *also)
+{
+    uint16_t *col16 = reinterpret_cast<uint16_t *>(&sh.seg[0][0][0]);  // colour of each rank
+    uint32_t *F = reinterpret_cast<uint32_t *>(col16 + kCoreMax);      // 32 forbidden sets of Fw words
+    const int Fw = (H + 2 + 31) / 32;                                   // colours 0..H+1
+    static_assert(sizeof(sh.seg) >= kCoreMax * 2 + 32 * ((kCoreMax + 2 + 31) / 32) * 4, "core sets fit");
+    const uint32_t *bits = reinterpret_cast<const uint32_t *>(p.wl[1]);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 32 * Fw; i += kBlock) F[i] = 0u;
+    int M = 0;
+    __syncthreads();
+    for (int b = 0; 32 * b < H; ++b) {
+        const int nb = min(32, H - 32 * b);
+        if (lane < nb) {
+            const int r = 32 * b + lane;
+            uint32_t *Fl = F + lane * Fw;
+            for (int w = wid; w < b; w += kWarps) {
+                uint32_t x = __ldcg(bits + (size_t)w * H + r);
+                while (x) {
+                    const int j = 32 * w + __ffs(x) - 1;
+                    x &= x - 1;
+                    const int c = col16[j];
+                    atomicOr(Fl + (c >> 5), 1u << (c & 31));
+                }
+            }
+        }
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t inb = lane < nb ? __ldcg(bits + (size_t)b * H + 32 * b + lane) : 0u;
+            int mine = 0;
+            for (int k = 0; k < nb; ++k) {
+                if (lane < k && ((inb >> k) & 1u)) atomicOr(F + k * Fw + (mine >> 5), 1u << (mine & 31));
+                __syncwarp();
+                int c = 0;
+                for (int w0 = 0; c == 0 && w0 < Fw; w0 += 32) {
+                    const int w = w0 + lane;
+                    uint32_t fr = w < Fw ? ~F[k * Fw + w] : 0u;
+                    if (w == 0) fr &= ~1u;  // colour 0 is not a colour
+                    const unsigned bal = __ballot_sync(FULL_MASK, fr != 0u);
+                    if (bal) {
+                        const int src = __ffs(bal) - 1;
+                        const uint32_t fb = __shfl_sync(FULL_MASK, fr, src);
+                        c = (w0 + src) * 32 + __ffs(fb) - 1;
+                    }
+                }
+                if (lane == k) mine = c;
+            }
+            if (lane < nb) {
+                col16[32 * b + lane] = (uint16_t)mine;
+                const int32_t v = __ldcg(p.mid_all + 32 * b + lane);
+                st_color<true>(p.cA + v, mine);
+                if (also) st_color<true>(also + v, mine);
+            }
+            const int bm = __reduce_max_sync(FULL_MASK, mine);
+            if (lane == 0) sh.claim = max(M, bm);
+        }
+        __syncthreads();
+        M = sh.claim;
+        // every set bit of the forbidden sets is a colour <= M: clear those words
+        const int fw = min(Fw, (M >> 5) + 1);
+        for (int i = threadIdx.x; i < 32 * fw; i += kBlock) F[(i / fw) * Fw + (i % fw)] = 0u;
+        __syncthreads();
+    }
+    return M;
+}
+
+
 template <bool ASYNC, bool BATCH>
 __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 {
@@ -1853,13 +2082,14 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
 #pragma unroll
             for (int u = 0; u < kProU; ++u) {
                 const long long vi = b0 + u * stride + threadIdx.x;
-                bool hub = false, midv = false;
+                bool hub = false, midv = false, corev = false;
                 const int32_t v = (int32_t)vi;
                 if (vi < p.n) {
                     const int64_t deg = degs[u];
                     const int32_t g = gs[u];
                     hub = deg > p.t2;
                     midv = tiers && !hub && deg > p.t1;
+                    corev = hub && p.core_deg > 0 && deg > p.core_deg;
                     if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
                     if (ASYNC && !hub && deg > kT1Max && __ldcg(&p.gstat[g].wide) == 0u)
                         atomicOr(&p.gstat[g].wide, 1u);
@@ -1868,15 +2098,29 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                     if (!ASYNC) mb += 4;
                     if (keep) p.mark[v] = 0;
                 }
-                const unsigned m = __ballot_sync(FULL_MASK, hub);
+                const unsigned m = __ballot_sync(FULL_MASK, hub && !corev);
                 if (m) {
                     const int leader = __ffs(m) - 1;
                     int ob = 0;
                     if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
                     ob = __shfl_sync(FULL_MASK, ob, leader);
-                    if (hub) {
+                    if (hub && !corev) {
                         const int o = ob + __popc(m & ((1u << lane) - 1u));
                         if (o < p.hub_cap) __stcg(p.hub_all + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    }
+                }
+                // core candidates: listed apart (coloured first if they fit,
+                // else taken by the hub pass after hub_all)
+                const unsigned mc = __ballot_sync(FULL_MASK, corev);
+                if (mc) {
+                    const int leader = __ffs(mc) - 1;
+                    int ob = 0;
+                    if (lane == leader) ob = atomicAdd(&st->core_count, __popc(mc));
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (corev) {
+                        const int o = ob + __popc(mc & ((1u << lane) - 1u));
+                        if (o < p.n) __stcg(p.mid_all + o, v);
                         else atomicOr(&st->error, GC_EW_OVERFLOW);
                     }
                 }
@@ -1988,13 +2232,48 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // Tile window for the round-0 pass over the graphs that are not
         // coloured in id order by one warp (window > 1 only).
         const int window = p.window > 1 ? p.window : -1;
+        int core_n = 0;
         if (ASYNC && alive && !recolor) {
+            // The core (see core_sort): sorted and marked by block 0 while the
+            // other blocks clear its bit matrix.
+            if (!BATCH && p.core_deg > 0) {
+                const int H = ld_volatile(&st->core_count);
+                const int W = (H + 31) / 32;
+                if (H > 0 && H <= kCoreMax && (long long)H * W <= (long long)p.n) {
+                    core_n = H;
+                    if (blockIdx.x == 0) core_sort(p, sh, H);
+                    if (nbl == 1 || blockIdx.x > 0) {
+                        const long long words = (long long)H * W;
+                        const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
+                        const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
+                        for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
+                    }
+                } else if (H > 0) {
+                    // too many for a core: ordinary hubs, appended to the hub list
+                    const int h0 = ld_volatile(&st->hub_all_count);
+                    for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < H; i += (long long)nbl * kBlock)
+                        if (h0 + i < p.hub_cap) __stcg(p.hub_all + h0 + i, __ldcg(p.mid_all + i));
+                }
+            }
             // Ids of a naturally numbered mesh are local: neighbours would be
             // coloured concurrently unless the graph goes strictly in id order.
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
             grid_sync(st, nbl);
             alive = ld_volatile(&st->error) == 0;
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
+            if (core_n > 0 && alive) {
+                core_build(p, core_n, mb);
+                grid_sync(st, nbl);
+                if (blockIdx.x == 0) {
+                    const int M = core_colour(p, sh, core_n, snap ? p.cB : nullptr);
+                    if (threadIdx.x == 0) {
+                        st->core_n = core_n;
+                        st->core_colors = M;
+                    }
+                }
+                grid_sync(st, nbl);
+                alive = ld_volatile(&st->error) == 0;
+            }
         }
 
         // Stages: one (all of V), or, with tiers, hubs -> mid degree -> low
@@ -2010,7 +2289,9 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             stages[2] = PassIn{true, nullptr, p.n, nullptr, 0, p.t1};
             nstages = 3;
         } else {
-            stages[0] = PassIn{true, nullptr, p.n, p.hub_all, hub_all_n, p.t2};
+            // core candidates that were not coloured as a core joined the hub list
+            const int extra = (!BATCH && p.core_deg > 0 && core_n == 0) ? ld_volatile(&st->core_count) : 0;
+            stages[0] = PassIn{true, nullptr, p.n, p.hub_all, hub_all_n + extra, p.t2};
         }
 
         int32_t *R = p.cA;

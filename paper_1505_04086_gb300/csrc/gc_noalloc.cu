@@ -118,7 +118,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     const int32_t t1 = o.t1 > 0 ? o.t1 : 32, t2 = o.t2 > 0 ? o.t2 : gc::default_t2(mode), tile = o.tile > 0 ? o.tile : 64;
     const int32_t tail = o.tail > 0 ? o.tail : (o.tail < 0 ? -1 : 2048);
     if (t1 > gc::kT1Max || t2 > gc::kT2Max || t1 > t2 || tile % 32 != 0 || tile > 4096 ||
-        o.blocks_per_sm < 0 || o.window < -1)
+        o.blocks_per_sm < 0 || o.window < -1 || o.core_deg < -1)
         return GC_ERR_ARG;
     gc_stats s;
     memset(&s, 0, sizeof s);
@@ -182,6 +182,8 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     p.tile = tile;
     p.tail = tail;
     p.window = o.window;
+    p.core_deg = gc::core_applies(mode, false, false) ? (o.core_deg > 0 ? o.core_deg : (o.core_deg < 0 ? 0 : gc::kCoreDeg))
+                                                      : 0;
 
     const bool async = (mode & GC_SCHED_ASYNC) != 0;
     const int occ = d->occ[async ? 1 : 0];

@@ -76,7 +76,8 @@ class gc_stats(ctypes.Structure):
 class gc_opts(ctypes.Structure):
     _fields_ = [("max_rounds", ctypes.c_int32), ("t1", ctypes.c_int32), ("t2", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("tail", ctypes.c_int32), ("window", ctypes.c_int32), ("d2_heavy", ctypes.c_int32)]
+                ("tail", ctypes.c_int32), ("window", ctypes.c_int32), ("d2_heavy", ctypes.c_int32),
+                ("core_deg", ctypes.c_int32)]
 
 
 class gc_batch(ctypes.Structure):

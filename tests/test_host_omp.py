@@ -69,13 +69,51 @@ def test_host_async_is_a_proper_colouring(g, alg, tie):
 
 def test_host_mode_bits_are_checked():
     g = I.kuhn3d(3)
-    for bad in (gc.GC_VALIDATE, gc.GC_DEBUG_NO_TIEBREAK, gc.GC_REPAIR_SNAPSHOT, gc.GC_TIERS, gc.GC_FF_KEEPERS,
-                1 << 20):
+    for bad in (gc.GC_DEBUG_NO_TIEBREAK, gc.GC_REPAIR_SNAPSHOT, gc.GC_TIERS, gc.GC_FF_KEEPERS, 1 << 20):
         rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, ASYNC | bad, 2)
         assert rc == gc.GC_ERR_ARG, bad
     rc, _, _ = gc.gc_host_color(g.row_ptr, g.col_idx, 0, -1)
     assert rc == gc.GC_ERR_ARG
     assert gc.gc_host_threads() >= 1
+
+
+def _malformed():
+    """(name, row_ptr, col_idx) of inputs GC_VALIDATE must reject."""
+    g = I.kuhn3d(3)
+    rp, ci = g.row_ptr.copy(), g.col_idx.copy()
+    unsorted = ci.copy()
+    unsorted[rp[5]], unsorted[rp[5] + 1] = unsorted[rp[5] + 1], unsorted[rp[5]]
+    out_of_range = ci.copy()
+    out_of_range[3] = g.n + 5
+    negative = ci.copy()
+    negative[0] = -1
+    selfloop = I.from_edges(3, [(0, 1), (1, 2)])
+    sl_ci = selfloop.col_idx.copy()
+    sl_ci[0] = 0  # vertex 0's entry 1 becomes 0: a self-loop
+    asym = I.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    as_ci = asym.col_idx.copy()
+    as_ci[-1] = 0  # vertex 3's neighbour 2 becomes 0, which does not list 3
+    bad_rp = rp.copy()
+    bad_rp[4] = bad_rp[6]  # row pointers decrease
+    bad_end = rp.copy()
+    bad_end[-1] -= 1
+    return [("unsorted", rp, unsorted), ("out_of_range", rp, out_of_range), ("negative", rp, negative),
+            ("selfloop", selfloop.row_ptr, sl_ci), ("asymmetric", asym.row_ptr, as_ci),
+            ("decreasing_row_ptr", bad_rp, ci), ("row_ptr_end", bad_end, ci)]
+
+
+@pytest.mark.parametrize("case", _malformed(), ids=lambda c: c[0])
+def test_host_validate_rejects_malformed_input(case):
+    name, rp, ci = case
+    rc, _, _ = gc.gc_host_color(rp, ci, ASYNC | gc.GC_VALIDATE, 2)
+    assert rc == gc.GC_ERR_GRAPH, name
+
+
+def test_host_validate_accepts_well_formed_input():
+    for g in GRAPHS:
+        rc, col, _ = gc.gc_host_color(g.row_ptr, g.col_idx, ASYNC | gc.GC_VALIDATE, 2)
+        assert rc == gc.GC_OK
+        assert O.check(g, col)[0] == 0
 
 
 D2_GRAPHS = [I.from_edges(7, [(i, i + 1) for i in range(6)]), I.from_edges(40, [(0, i) for i in range(1, 40)]),
