@@ -582,6 +582,38 @@ int gc_host_threads(void);
  */
 int gc_debug_barrier_timeout(int device, int32_t timeout_ms, int32_t *error_word_out);
 
+/* The bounded waits of the colouring kernel that gc_debug_wait_timeout can
+ * run out. */
+enum {
+    GC_WAIT_GRID_BARRIER = 0,    /* the grid barrier between rounds (10 s) */
+    GC_WAIT_TILE_DONE = 1,       /* asynchronous round 0 with gc_opts.window >
+                                    1: a tile waits until the tile `window`
+                                    places before it is published (10 s) */
+    GC_WAIT_PIPE_CHUNK = 2,      /* round 0 of a graph coloured in id order by
+                                    a group of warps: a vertex waits until its
+                                    lower neighbours are coloured (2 s) */
+    GC_WAIT_STAGE_COPY = 3       /* a staged adjacency copy (TMA bulk copy)
+                                    completing on its mbarrier (2 s, then as
+                                    long again for the copy to land) */
+};
+
+/*
+ * Check of one bounded wait of the colouring kernel, as
+ * gc_debug_barrier_timeout does for the grid barrier: a one-warp launch on
+ * `device` runs that wait against a flag nobody publishes (GC_WAIT_TILE_DONE),
+ * a lower neighbour nobody colours (GC_WAIT_PIPE_CHUNK; a 64-vertex graph
+ * whose vertex 32 is adjacent to vertex 0) or an mbarrier no copy completes
+ * (GC_WAIT_STAGE_COPY), with the limit timeout_ms (1..10000) instead of the
+ * one given above.  The wait gives up, the device error word receives
+ * GC_EW_TIMEOUT (copied to *error_word_out if not NULL) and the kernel
+ * returns; the CUDA context stays usable.  GC_WAIT_STAGE_COPY waits twice the
+ * limit (the second wait lets a copy in flight land).  Synchronous.  Returns
+ * GC_ERR_TIMEOUT when the wait ran out as it should, GC_OK if it did not,
+ * GC_ERR_ARG or GC_ERR_CUDA.  GC_WAIT_GRID_BARRIER is
+ * gc_debug_barrier_timeout.
+ */
+int gc_debug_wait_timeout(int device, int32_t wait, int32_t timeout_ms, int32_t *error_word_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,7 +86,10 @@ __device__ __forceinline__ void st_color(int32_t *p, int v)
 // All nblocks blocks must be co-resident (cooperative launch).  A block that
 // waits longer than timeout_ns (default 10 s) sets GC_EW_TIMEOUT and leaves; the
 // caller checks the error word after every barrier.
-static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long long timeout_ns = kBarrierTimeoutNs)
+// sleep_ns: pause between polls; a long one where the grid waits for one
+// block's serial work keeps the polls from crowding that block's L2 traffic.
+static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long long timeout_ns = kBarrierTimeoutNs,
+                                 unsigned sleep_ns = 64)
 {
     PT_BEGIN(t_bar);
     __syncthreads();
@@ -103,7 +106,7 @@ static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long l
                 unsigned long long t0 = global_timer();
                 unsigned polls = 0;
                 while (ld_acquire_u32(&st->bar_gen) == gen) {
-                    __nanosleep(64);
+                    __nanosleep(sleep_ns);
                     if (++polls > kBarrierMaxPolls || global_timer() - t0 > timeout_ns) {
                         atomicOr(&st->error, GC_EW_TIMEOUT);
                         break;

@@ -196,6 +196,9 @@ cudaError_t launch_check(const KParams &p, bool batch, int grid, cudaStream_t s)
 cudaError_t launch_color_d2(const KParams &p, bool async, int grid, cudaStream_t s);
 cudaError_t query_occupancy_d2(bool async, int *blocks_per_sm);
 cudaError_t launch_check_d2(const KParams &p, int grid, cudaStream_t s);
+// Failure-path probe (gc_kernels.cu): one bounded wait (GC_WAIT_TILE_DONE,
+// GC_WAIT_PIPE_CHUNK or GC_WAIT_STAGE_COPY) run out against p's state.
+cudaError_t launch_wait_probe(const KParams &p, int which, unsigned long long timeout_ns, cudaStream_t s);
 cudaError_t launch_build_lut(const int64_t *vtx_off, int32_t G, int32_t n, int32_t *lut,
                              cudaStream_t s);
 

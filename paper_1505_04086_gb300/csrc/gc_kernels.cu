@@ -910,8 +910,10 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     return suspect;
 }
 
-// Wait (bounded) until tile t of the ordered pass has been published.
-__device__ void wait_tile_done(const KParams &p, long long t, int lane)
+// Wait (bounded: timeout_ns, 10 s by default) until tile t of the ordered
+// pass has been published.
+__device__ void wait_tile_done(const KParams &p, long long t, int lane,
+                               unsigned long long timeout_ns = kBarrierTimeoutNs)
 {
     if (lane == 0) {
         const unsigned *f = reinterpret_cast<const unsigned *>(p.done + t);
@@ -919,7 +921,7 @@ __device__ void wait_tile_done(const KParams &p, long long t, int lane)
         unsigned polls = 0;
         while (ld_acquire_u32(f) == 0u) {
             __nanosleep(32);
-            if (++polls > kBarrierMaxPolls || global_timer() - t0 > kBarrierTimeoutNs) {
+            if (++polls > kBarrierMaxPolls || global_timer() - t0 > timeout_ns) {
                 atomicOr(&p.st->error, GC_EW_TIMEOUT);
                 break;
             }
@@ -1021,7 +1023,7 @@ struct LaneRow {
     int32_t nbase, g;          // batch: graph offset and graph (0 otherwise)
 };
 
-constexpr unsigned kStagePolls = 1u << 22;
+constexpr unsigned long long kStageTimeoutNs = 2000000000ull;  // 2 s for one staged copy
 
 // Load the lanes' row pointers of chunk [cb, min(cb+32, cend)) into `r`,
 // record the chunk in Shared::slot[wid][slot] and start the 1-D TMA copy of
@@ -1070,23 +1072,34 @@ __device__ __forceinline__ void stage_chunk(const KParams &p, Shared &sh, long l
     __syncwarp();
 }
 
-// Bounded wait for the copy into seg[wid][slot]; on timeout the error word
-// gets GC_EW_TIMEOUT and the copy is waited for once more (bounded) so that
-// it does not land after the block has moved on.
-__device__ __forceinline__ bool wait_stage(const KParams &p, Shared &sh, int slot, uint32_t &phase, int wid)
+// Bounded wait for phase `par` of mbarrier `bar` (the completion of a
+// staged copy): gives up after timeout_ns, setting GC_EW_TIMEOUT, and then
+// waits once more, as long again, so that a copy still in flight does not
+// land after the caller has moved on.  False on timeout.
+__device__ __noinline__ bool wait_mbar(const KParams &p, unsigned long long *bar, uint32_t par,
+                                       unsigned long long timeout_ns)
 {
-    const uint32_t par = (phase >> slot) & 1u;
-    phase ^= 1u << slot;
-    unsigned polls = 0;
-    while (!mbar_try_wait(&sh.mbar[wid][slot], par)) {
-        if (++polls > kStagePolls) {
+    const unsigned long long t0 = global_timer();
+    while (!mbar_try_wait(bar, par)) {
+        if (global_timer() - t0 > timeout_ns) {
             atomicOr(&p.st->error, GC_EW_TIMEOUT);
-            for (unsigned k = 0; k < kStagePolls && !mbar_try_wait(&sh.mbar[wid][slot], par); ++k) {
+            const unsigned long long t1 = global_timer();
+            while (!mbar_try_wait(bar, par) && global_timer() - t1 <= timeout_ns) {
             }
             return false;
         }
     }
     return true;
+}
+
+// Wait for the copy into seg[wid][slot] (see wait_mbar).
+__device__ __forceinline__ bool wait_stage(const KParams &p, Shared &sh, int slot, uint32_t &phase, int wid)
+{
+    const uint32_t par = (phase >> slot) & 1u;
+    phase ^= 1u << slot;
+    for (int k = 0; k < 1024; ++k)  // each try suspends the thread a while in hardware
+        if (mbar_try_wait(&sh.mbar[wid][slot], par)) return true;
+    return wait_mbar(p, &sh.mbar[wid][slot], par, kStageTimeoutNs);
 }
 
 // Round 0 of an ordered graph (ids v0..v1-1): one warp colours it chunk by
@@ -1199,7 +1212,8 @@ constexpr unsigned long long kPipeTimeoutNs = 2000000000ull;  // 2 s per chunk
 // Returns false if a wait timed out (error word set).
 template <class E>
 __device__ bool chunk_pipe(const KParams &p, const E &ent, int32_t cb, int32_t v, int64_t beg, int deg,
-                           int32_t nbase, int32_t *C, long long &mb, int lane)
+                           int32_t nbase, int32_t *C, long long &mb, int lane,
+                           unsigned long long timeout_ns = kPipeTimeoutNs)
 {
     const bool act = v >= 0;
     unsigned done = __ballot_sync(FULL_MASK, !act);
@@ -1269,7 +1283,7 @@ __device__ bool chunk_pipe(const KParams &p, const E &ent, int32_t cb, int32_t v
         // nothing can go: the group's other warps still colour lower ids
         if (t0 == 0) {
             t0 = global_timer();
-        } else if (global_timer() - t0 > kPipeTimeoutNs) {
+        } else if (global_timer() - t0 > timeout_ns) {
             if (lane == 0) atomicOr(&p.st->error, GC_EW_TIMEOUT);
             return false;
         }
@@ -1912,19 +1926,56 @@ __device__ __noinline__ void core_build(const KParams &p, int H, long long &mb)
     }
 }
 
+// The 64 colours f, f+1, ..., f+63 of forbidden set Fl (Fw words) as a
+// mask of the free ones (bit i: colour f+i is free).
+__device__ __forceinline__ unsigned long long free_window(const uint32_t *Fl, int Fw, int f)
+{
+    const int w = f >> 5, sh = f & 31;
+    const unsigned long long a = w < Fw ? Fl[w] : 0u;
+    const unsigned long long b = w + 1 < Fw ? Fl[w + 1] : 0u;
+    const unsigned long long c = w + 2 < Fw ? Fl[w + 2] : 0u;
+    const unsigned long long lo = a | (b << 32), hi = c;
+    const unsigned long long taken = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+    return ~taken;
+}
+
+// First colour >= 1 not in the forbidden set Fl; warp-wide (every lane
+// gets it).
+__device__ __forceinline__ int first_free_warp(const uint32_t *Fl, int Fw, int lane)
+{
+    for (int w0 = 0; w0 < Fw; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t fr = w < Fw ? ~Fl[w] : 0u;
+        if (w == 0) fr &= ~1u;  // colour 0 is not a colour
+        const unsigned bal = __ballot_sync(FULL_MASK, fr != 0u);
+        if (bal) {
+            const int src = __ffs(bal) - 1;
+            const uint32_t fb = __shfl_sync(FULL_MASK, fr, src);
+            return (w0 + src) * 32 + __ffs(fb) - 1;
+        }
+    }
+    return Fw * 32;  // not reached: Fw words cover colours up to H+1
+}
+
 // Block 0: sequential First-Fit over the core in rank order, 32 ranks at a
-// time: first every vertex of the batch collects the colours of its core
-// neighbours in earlier batches (all warps, bits of the matrix), then warp 0
-// resolves the batch in rank order (each vertex also avoids the colours just
-// given to its lower-ranked neighbours in the batch).  The colours go to
-// p.cA and, if not null, to `also` (the second buffer of snapshot repairs,
-// which only inspected vertices are written to).  Returns the largest colour.
+// time.  First every vertex of the batch collects in its forbidden set the
+// colours of its core neighbours in earlier batches (all warps; the bit
+// words of a thread are loaded together).  Then warp 0 resolves the batch
+// in rank order: a vertex takes the first colour that is neither forbidden
+// nor given to a lower-ranked neighbour of the batch.  Each lane keeps the 64
+// colours from its first free one as a register mask, and lane k's choice is
+// removed from the masks of its neighbours above it (one shuffle per rank);
+// should a mask run empty (the answer lies further up), the batch is
+// resolved again word by word.  The colours go to p.cA and, if not null, to
+// `also` (the second buffer of snapshot repairs, which only inspected
+// vertices are written to).  Returns the largest colour.
 __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int32_t *also)
 {
     uint16_t *col16 = reinterpret_cast<uint16_t *>(&sh.seg[0][0][0]);  // colour of each rank
     uint32_t *F = reinterpret_cast<uint32_t *>(col16 + kCoreMax);      // 32 forbidden sets of Fw words
     const int Fw = (H + 2 + 31) / 32;                                   // colours 0..H+1
     static_assert(sizeof(sh.seg) >= kCoreMax * 2 + 32 * ((kCoreMax + 2 + 31) / 32) * 4, "core sets fit");
+    constexpr int kWordsPerThread = (kCoreMax / 32 + kWarps - 1) / kWarps;
     const uint32_t *bits = reinterpret_cast<const uint32_t *>(p.wl[1]);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 32 * Fw; i += kBlock) F[i] = 0u;
@@ -1935,12 +1986,19 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
         if (lane < nb) {
             const int r = 32 * b + lane;
             uint32_t *Fl = F + lane * Fw;
-            for (int w = wid; w < b; w += kWarps) {
-                uint32_t x = __ldcg(bits + (size_t)w * H + r);
+            uint32_t xs[kWordsPerThread];
+#pragma unroll
+            for (int q = 0; q < kWordsPerThread; ++q) {
+                const int w = wid + q * kWarps;
+                xs[q] = w < b ? __ldcg(bits + (size_t)w * H + r) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < kWordsPerThread; ++q) {
+                uint32_t x = xs[q];
+                const int base = 32 * (wid + q * kWarps);
                 while (x) {
-                    const int j = 32 * w + __ffs(x) - 1;
+                    const int c = col16[base + __ffs(x) - 1];
                     x &= x - 1;
-                    const int c = col16[j];
                     atomicOr(Fl + (c >> 5), 1u << (c & 31));
                 }
             }
@@ -1948,23 +2006,37 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
         __syncthreads();
         if (wid == 0) {
             const uint32_t inb = lane < nb ? __ldcg(bits + (size_t)b * H + 32 * b + lane) : 0u;
+            const uint32_t *Fl = F + lane * Fw;
+            // first free colour of each lane's set, then its 64-colour window
+            int f = 1;
+            if (lane < nb) {
+                int w = 0;
+                uint32_t fr = ~Fl[0] & ~1u;
+                while (fr == 0u && w + 1 < Fw) fr = ~Fl[++w];
+                f = w * 32 + __ffs(fr) - 1;
+            }
+            unsigned long long m = lane < nb ? free_window(Fl, Fw, f) : 1ull;
             int mine = 0;
+            bool empty = false;
             for (int k = 0; k < nb; ++k) {
-                if (lane < k && ((inb >> k) & 1u)) atomicOr(F + k * Fw + (mine >> 5), 1u << (mine & 31));
-                __syncwarp();
-                int c = 0;
-                for (int w0 = 0; c == 0 && w0 < Fw; w0 += 32) {
-                    const int w = w0 + lane;
-                    uint32_t fr = w < Fw ? ~F[k * Fw + w] : 0u;
-                    if (w == 0) fr &= ~1u;  // colour 0 is not a colour
-                    const unsigned bal = __ballot_sync(FULL_MASK, fr != 0u);
-                    if (bal) {
-                        const int src = __ffs(bal) - 1;
-                        const uint32_t fb = __shfl_sync(FULL_MASK, fr, src);
-                        c = (w0 + src) * 32 + __ffs(fb) - 1;
-                    }
+                const int cand = m ? f + __ffsll((long long)m) - 1 : 0;
+                const int ck = __shfl_sync(FULL_MASK, cand, k);
+                if (lane == k) {
+                    mine = ck;
+                    empty = (m == 0ull);
                 }
-                if (lane == k) mine = c;
+                const unsigned d = (unsigned)(ck - f);
+                if (lane > k && ((inb >> k) & 1u) && d < 64u) m &= ~(1ull << d);
+            }
+            if (__any_sync(FULL_MASK, empty)) {
+                // exact fallback: word-by-word search in rank order
+                mine = 0;
+                for (int k = 0; k < nb; ++k) {
+                    if (lane < k && ((inb >> k) & 1u)) atomicOr(F + k * Fw + (mine >> 5), 1u << (mine & 31));
+                    __syncwarp();
+                    const int c = first_free_warp(F + k * Fw, Fw, lane);
+                    if (lane == k) mine = c;
+                }
             }
             if (lane < nb) {
                 col16[32 * b + lane] = (uint16_t)mine;
@@ -2258,7 +2330,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             // Ids of a naturally numbered mesh are local: neighbours would be
             // coloured concurrently unless the graph goes strictly in id order.
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
-            grid_sync(st, nbl);
+            grid_sync(st, nbl, kBarrierTimeoutNs, core_n > 0 ? 512 : 64);
             alive = ld_volatile(&st->error) == 0;
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
             if (core_n > 0 && alive) {
@@ -2271,7 +2343,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                         st->core_colors = M;
                     }
                 }
-                grid_sync(st, nbl);
+                grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for block 0's serial work
                 alive = ld_volatile(&st->error) == 0;
             }
         }
@@ -2500,6 +2572,48 @@ __global__ void build_lut_kernel(const int64_t *vtx_off, int32_t G, int32_t n, i
         const int64_t block_end = x + (1ll << kLutShift) < (int64_t)n ? x + (1ll << kLutShift) : (int64_t)n;
         lut[c] = (lo + 1 >= G || vtx_off[lo + 1] >= block_end) ? -lo - 1 : lo;  // negative: one graph only
     }
+}
+
+// ------------------------------------------------------------------------
+// failure-path probes (gc_debug_wait_timeout)
+// ------------------------------------------------------------------------
+
+// One bounded wait of the colouring kernel run against something that never
+// happens, with a short limit; the wait must give up, set GC_EW_TIMEOUT and
+// return.  One warp.
+//   GC_WAIT_TILE_DONE:  an ordered round-0 tile flag nobody publishes (p.done
+//                       zeroed);
+//   GC_WAIT_PIPE_CHUNK: a warp-group chunk whose lane 0 (vertex 32) has a
+//                       lower neighbour (vertex 0) that no warp colours
+//                       (p.row_ptr/p.col_idx: that graph, p.cA zeroed);
+//   GC_WAIT_STAGE_COPY: a staged-copy barrier that no copy completes (an
+//                       mbarrier expecting one arrival that never comes).
+__global__ void wait_probe_kernel(KParams p, int which, unsigned long long timeout_ns)
+{
+    __shared__ unsigned long long bar;
+    const int lane = threadIdx.x & 31;
+    if (which == GC_WAIT_TILE_DONE) {
+        wait_tile_done(p, 0, lane, timeout_ns);
+    } else if (which == GC_WAIT_PIPE_CHUNK) {
+        const int32_t v = 32 + lane;
+        const int32_t beg = __ldg(p.row_ptr + v), end = __ldg(p.row_ptr + v + 1);
+        long long mb = 0;
+        chunk_pipe(p, GlobalEnts{p.col_idx}, 32, v, beg, end - beg, 0, p.cA, mb, lane, timeout_ns);
+    } else if (which == GC_WAIT_STAGE_COPY) {
+        if (lane == 0) {
+            mbar_init(&bar, 1);
+            fence_mbarrier_init();
+        }
+        __syncwarp();
+        if (lane == 0) wait_mbar(p, &bar, 0, timeout_ns);
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_wait_probe(const KParams &p, int which, unsigned long long timeout_ns, cudaStream_t s)
+{
+    wait_probe_kernel<<<1, 32, 0, s>>>(p, which, timeout_ns);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------

@@ -59,6 +59,11 @@ GC_EW_OVERFLOW = 4
 GC_EW_GRAPH = 8
 GC_EW_CHECK = 16
 
+GC_WAIT_GRID_BARRIER = 0
+GC_WAIT_TILE_DONE = 1
+GC_WAIT_PIPE_CHUNK = 2
+GC_WAIT_STAGE_COPY = 3
+
 
 class gc_csr(ctypes.Structure):
     _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
@@ -141,6 +146,8 @@ _SIGS = {
                                      ctypes.c_int32, _P, ctypes.POINTER(gc_stats)]),
     "gc_host_threads": (ctypes.c_int, []),
     "gc_debug_barrier_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "gc_debug_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32)]),
 }
 
 _lock = threading.Lock()
@@ -424,6 +431,14 @@ def gc_host_color(row_ptr, col_idx, mode: int = 0, num_threads: int = 0, round_c
     rc = load().gc_host_color(ctypes.byref(csr), int(n), int(ci.size), int(mode), int(num_threads),
                               col.ctypes.data, ctypes.byref(st))
     return int(rc), col[:n], stats_dict(st, rs, rn)
+
+
+def gc_debug_wait_timeout(device: int = 0, wait: int = 0, timeout_ms: int = 200):
+    """Run one bounded wait of the colouring kernel (GC_WAIT_*) against
+    something that never happens; returns (status, device error word)."""
+    w = ctypes.c_int32(0)
+    rc = load().gc_debug_wait_timeout(int(device), int(wait), int(timeout_ms), ctypes.byref(w))
+    return int(rc), int(w.value)
 
 
 def gc_debug_barrier_timeout(device: int = 0, timeout_ms: int = 200):
