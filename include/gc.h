@@ -395,6 +395,14 @@ typedef struct {
  * colourings while it runs.  In GC_SCHED_DET mode every option set gives
  * the same colouring, so only speed is at stake.  Returns the first error
  * of any run.
+ *
+ * Cache: when the environment variable GC_TUNE_CACHE names a file, results
+ * are kept there (one text line each, appended) under a key of the library
+ * version, the call, the mode, the graph's shape (total vertices, entries,
+ * graphs), the device's SM count and reps.  A call whose key is in the file
+ * searches nothing: it colours once with the cached options (colors_out
+ * receives that colouring) and returns them with evaluated = 0 and the
+ * cached times.
  */
 int gc_autotune_batch(gc_ctx *ctx, const gc_batch *batch, uint32_t mode, int32_t reps, int32_t *colors_out,
                       gc_tune_result *result);
@@ -431,10 +439,13 @@ int gc_color_classes(gc_ctx *ctx, const int32_t *colors, int32_t n, int32_t num_
  * A colouring server on one device.  Requests (graphs in host memory) are
  * queued; a worker thread admits them in arrival order while their CSR fits
  * the device-memory budget (and at most max_slots are resident), uploading
- * them on a copy stream, and whenever the GPU is free it colours all
- * uploaded requests in one batched launch (gc_color_batch semantics, every
- * graph independent).  Requests that arrive while a batch runs are uploaded
- * meanwhile and join the next batch.  Thread-safe.
+ * them on a copy stream, and colours the uploaded requests in batched
+ * launches ("waves", gc_color_batch semantics, every graph independent) on
+ * two compute lanes: a wave starts as soon as a lane is free, so requests
+ * that arrive while a wave runs are coloured in the next wave on the other
+ * lane, beside it.  Each wave's grid takes its share of the SMs (opts
+ * blocks_per_sm, by default half the kernel's resident blocks per SM).
+ * Thread-safe.
  *
  * Memory: the budget is one device allocation holding the resident graphs'
  * row pointers and column indices ((n+1+nnz)*4 bytes each, 256-byte
@@ -456,7 +467,13 @@ typedef struct {
     int32_t queued;              /* waiting for admission */
     int32_t resident;            /* admitted and not finished */
     int32_t max_wave_graphs;     /* largest batch launched */
-    int32_t pad;
+    int32_t lanes;               /* waves that can be on the GPU at once */
+    uint64_t cancelled;          /* requests dropped by gc_server_cancel */
+    uint64_t overlapped_waves;   /* waves whose GPU interval (event timestamps
+                                    around the colouring) overlapped another
+                                    lane's wave */
+    int64_t overlap_us;          /* total time two waves were on the GPU at
+                                    once (same timestamps) */
 } gc_server_info;
 
 /* Create a server on `device` with a device-memory budget and a slot limit;
@@ -480,6 +497,13 @@ int gc_server_poll(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats 
 /* As gc_server_poll, waiting up to timeout_ms (< 0: no limit) for the
  * request to finish; GC_PENDING if it has not. */
 int gc_server_wait(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats *stats_out, int32_t timeout_ms);
+
+/* Drop a request: a queued one is removed before any GPU work, one already
+ * uploading or being coloured is discarded when its work ends, a finished one
+ * is discarded unpolled.  The ticket is released at once (poll and wait then
+ * return GC_ERR_NOT_FOUND).  GC_OK, or GC_ERR_NOT_FOUND for an unknown
+ * ticket. */
+int gc_server_cancel(gc_server *s, uint64_t ticket);
 
 /* Counters and memory use of the server. */
 int gc_server_query(gc_server *s, gc_server_info *out);

@@ -20,6 +20,7 @@ LIB = os.path.join(PKG, "libgc.so")
 SOURCES = ["gc_kernels.cu", "gc_api.cu", "gc_noalloc.cu", "gc_server.cu", "gc_tune.cu", "gc_classes.cu", "gc_d2.cu",
            "gc_diag.cu", "gc_host.cpp"]
 HEADERS = [os.path.join(CSRC, "gc_internal.h"), os.path.join(CSRC, "gc_device.cuh"), os.path.join(CSRC, "gc_ctx.h"),
+           os.path.join(CSRC, "gc_nvtx.h"),
            os.path.join(INCLUDE, "gc.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -65,19 +66,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, defines=None, out: str | None = None,
-          build_dir: str | None = None) -> str:
-    """Compile (if needed) and return the path of libgc.so.  `defines`
-    (e.g. {"GC_THREAD_UNROLL": 16}), `out` and `build_dir` build a variant
-    library elsewhere (tuning experiments); the defaults build the product."""
-    lib = out or LIB
-    bdir = build_dir or BUILD
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile (if needed) and return the path of libgc.so."""
+    lib = LIB
+    bdir = BUILD
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                      "-I", INCLUDE, "-I", CSRC]
-    for k, v in (defines or {}).items():
-        common.append(f"-D{k}={v}")
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -13,6 +13,7 @@
 #include "gc.h"
 #include "gc_ctx.h"
 #include "gc_internal.h"
+#include "gc_nvtx.h"
 
 using gc::Buf;
 using gc::DevState;
@@ -385,6 +386,7 @@ void gc_ctx_destroy(gc_ctx *c)
 int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
                    int32_t *colors_out, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_color_async");
     if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
     if (!gc::mode_ok(mode)) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
@@ -422,6 +424,7 @@ int gc_color_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_
 int gc_recolor_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
                      int32_t *colors_inout, const int32_t *touched, int32_t n_touched, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_recolor_async");
     if (!c || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || n_touched < 0) return GC_ERR_ARG;
     if (!gc::dist1_mode_ok(mode) || (mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_REPAIR_SNAPSHOT))) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_inout)) return GC_ERR_ARG;
@@ -461,6 +464,7 @@ int gc_recolor_async(gc_ctx *c, const gc_csr *csr, int32_t n, int64_t nnz, uint3
 
 int gc_ctx_stats(gc_ctx *c, gc_stats *out)
 {
+    gc::NvtxRange nvtx_range("gc_ctx_stats");
     if (!c) return GC_ERR_ARG;
     if (!c->last.pending) return c->last.launch_status != GC_OK ? c->last.launch_status : GC_ERR_ARG;
     gc_stats s;
@@ -522,6 +526,7 @@ int gc_ctx_stats(gc_ctx *c, gc_stats *out)
 
 int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t *colors_out, gc_stats *stats_out)
 {
+    gc::NvtxRange nvtx_range("gc_color");
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
@@ -569,6 +574,7 @@ int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t *
 int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *opts, int32_t *colors_out,
                    int32_t *rounds_out, int64_t *conflicts_out, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_color_batch");
     if (!c || !b || b->G < 0 || b->total_n < 0 || b->total_n > INT32_MAX || b->total_nnz < 0 ||
         b->total_nnz >= (1ll << gc::kWorkBits))
         return GC_ERR_ARG;
@@ -580,14 +586,3 @@ int gc_color_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o
 }
 
 }  // extern "C"
-
-#ifdef GC_PHASE_TIMING
-// Tuning builds only: the phase cycle counters of the context's last call.
-extern "C" int gc_debug_phase_cycles(gc_ctx *c, unsigned long long *out16)
-{
-    if (!c || !out16) return GC_ERR_ARG;
-    if (cudaEventSynchronize(c->ev_done) != cudaSuccess) return GC_ERR_CUDA;
-    memcpy(out16, c->st_host->dbg, sizeof(c->st_host->dbg));
-    return GC_OK;
-}
-#endif

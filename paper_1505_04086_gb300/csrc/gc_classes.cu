@@ -18,6 +18,7 @@
 #include "gc.h"
 #include "gc_ctx.h"
 #include "gc_internal.h"
+#include "gc_nvtx.h"
 
 namespace gc {
 namespace {
@@ -166,6 +167,7 @@ __global__ void classes_bounds_kernel(int32_t *class_ptr, int32_t k, int32_t n)
 extern "C" int gc_color_classes(gc_ctx *c, const int32_t *colors, int32_t n, int32_t num_colors, int32_t *class_ptr,
                                 int32_t *class_vertices, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_color_classes");
     if (!c || n < 0 || num_colors < 0 || num_colors > GC_CLASSES_MAX_COLORS || !class_ptr ||
         (n > 0 && (!colors || !class_vertices)) || (n > 0 && num_colors < 1))
         return GC_ERR_ARG;

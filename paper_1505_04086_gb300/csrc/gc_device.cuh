@@ -10,19 +10,6 @@ namespace gc {
 
 #define FULL_MASK 0xffffffffu
 
-// Phase cycle accounting for tuning builds (-DGC_PHASE_TIMING): lane 0 of a
-// warp adds the clock64 cycles of a phase to DevState::dbg[slot].
-#ifdef GC_PHASE_TIMING
-#define PT_BEGIN(var) long long var = clock64()
-#define PT_END(st, slot, var)                                                          \
-    do {                                                                                \
-        if ((threadIdx.x & 31) == 0) atomicAdd(&(st)->dbg[slot], (unsigned long long)(clock64() - (var))); \
-    } while (0)
-#else
-#define PT_BEGIN(var)
-#define PT_END(st, slot, var)
-#endif
-
 constexpr unsigned long long kBarrierTimeoutNs = 10000000000ull;  // 10 s
 constexpr unsigned kBarrierMaxPolls = 1u << 28;
 
@@ -56,13 +43,10 @@ __device__ __forceinline__ int ld_volatile(const int *p) { return *(const volati
 // coherent (never served from a stale L1 line).  Deterministic mode never
 // reads a buffer that is written in the same round; it still bypasses L1
 // (.cg) because the buffer was written in an earlier round of this launch.
-#ifndef GC_ASYNC_LOAD
-#define GC_ASYNC_LOAD 0
-#endif
 template <bool ASYNC>
 __device__ __forceinline__ int ld_color(const int32_t *p)
 {
-    if (ASYNC && GC_ASYNC_LOAD == 0) {
+    if (ASYNC) {
         int v;
         asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
         return v;
@@ -91,7 +75,6 @@ __device__ __forceinline__ void st_color(int32_t *p, int v)
 static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long long timeout_ns = kBarrierTimeoutNs,
                                  unsigned sleep_ns = 64)
 {
-    PT_BEGIN(t_bar);
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -117,7 +100,6 @@ static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long l
         }
     }
     __syncthreads();
-    PT_END(st, 8, t_bar);
 }
 
 // Whether a clash of v with u is v's to repair: u keeps its colour (lower

@@ -30,6 +30,7 @@
 #endif
 
 #include "gc.h"
+#include "gc_nvtx.h"
 
 namespace {
 
@@ -261,6 +262,7 @@ extern "C" int gc_host_threads(void) { return threads_for(0); }
 extern "C" int gc_host_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t num_threads,
                              int32_t *colors_out, gc_stats *stats_out)
 {
+    gc::NvtxRange nvtx_range("gc_host_color");
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX || num_threads < 0 || (mode & ~kHostModes)) return GC_ERR_ARG;
     if (n > 0 && (!csr->row_ptr || !colors_out)) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;

@@ -15,10 +15,7 @@ constexpr int kT1Max = 62;              // thread path keeps colours in a 64-bit
 constexpr int kT2Max = 4096;            // warp path bitmap covers colours 0..kT2Max+1
 constexpr int kWarpBmWords = (kT2Max + 2) / 32 + 1;
 constexpr int kHubBmWords = 256;        // block path: 8192-colour window per pass
-#ifndef GC_SEG_CAP
-#define GC_SEG_CAP 512
-#endif
-constexpr int kSegCap = GC_SEG_CAP;     // staged adjacency entries per buffer (2 per warp)
+constexpr int kSegCap = 512;            // staged adjacency entries per buffer (2 per warp)
 constexpr int kRingIds = 1024;          // ordered graphs: colours of the last ids, per warp
 constexpr int kLutShift = 10;           // batch: graph lookup per 1024 vertices
 constexpr int kRing = 4;                // round-counter ring depth
@@ -106,7 +103,6 @@ struct DevState {
     // degrees (tile and hub lists), one atomic per push
     unsigned long long wl_packed[kRing];
     int distinct;
-    unsigned long long dbg[16];      // phase cycle counters (builds with GC_PHASE_TIMING only)
     int seq_claim;                   // round 0: next ordered graph to claim
     int n_ordered;                   // number of ordered graphs coloured by one warp
     int n_pitems;                    // warps of the groups colouring one graph in id order

@@ -112,16 +112,8 @@ __device__ __forceinline__ void row_of(const KParams &p, int32_t v, int64_t &beg
 // thread per vertex (deg <= t1 <= 62)
 // ------------------------------------------------------------------------
 
-#ifndef GC_THREAD_UNROLL
-#define GC_THREAD_UNROLL 8
-#endif
-#ifndef GC_MIN_BLOCKS
-#define GC_MIN_BLOCKS 3
-#endif
-constexpr int kUnroll = GC_THREAD_UNROLL;  // adjacency entries per thread in flight
-#ifndef GC_PASS_INLINE
-#define GC_PASS_INLINE __forceinline__
-#endif
+constexpr int kUnroll = 8;     // adjacency entries per thread in flight (thread path)
+constexpr int kMinBlocks = 3;  // launch bound: resident blocks per SM the register budget allows
 
 // Adjacency entry k (a global CSR index) of the row being processed: read
 // from col_idx, or from the warp's staged copy of the chunk's segment.
@@ -422,10 +414,7 @@ __device__ void push_clashes_warp(const KParams &p, int32_t v, int64_t beg, int6
 }
 
 constexpr int kWarpUnroll = 4;   // entries per lane in flight (warp path)
-#ifndef GC_BLOCK_UNROLL
-#define GC_BLOCK_UNROLL 4
-#endif
-constexpr int kBlockUnroll = GC_BLOCK_UNROLL;  // entries per thread in flight (block path)
+constexpr int kBlockUnroll = 4;  // entries per thread in flight (block path)
 
 template <bool ASYNC>
 __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
@@ -810,7 +799,6 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // gains nothing from the part of a row above v either.
     const bool keep = keepers || (RING && skip_higher);
     int nread = 0, nskip = 0;
-    PT_BEGIN(t_g);
     if (thr) {
         const auto row = ent.row(beg);
         for (int i = 0; i < deg; i += kUnroll) {
@@ -872,17 +860,13 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         }
     }
     __syncwarp();
-    PT_END(p.st, 6, t_g);
-    PT_BEGIN(t_r);
     const int mine = resolve_in_order(ext, low, thr, lane);
-    PT_END(p.st, 7, t_r);
     if (thr) {
         st_color<true>(C + v, mine);
         mb += 8 + 8ll * nread - 4ll * nskip + 4;  // index only for the unread colours
         if (zmask && p.r0mask) __stcg(reinterpret_cast<unsigned long long *>(p.r0mask) + v, zmask);
     }
     __syncwarp();
-    PT_BEGIN(t_mid);
     unsigned mm = midmask;
     while (mm) {
         const int src = __ffs(mm) - 1;
@@ -893,7 +877,6 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
         const int32_t nb = __shfl_sync(FULL_MASK, nbase, src);
         vertex_warp<true, false>(p, OP_TENT, vv, bb, ee, nb, C, C, true, mb, bm, lane, 0);
     }
-    PT_END(p.st, 5, t_mid);
     if (RING) {
         __syncwarp();
         if (v >= 0) {
@@ -1160,15 +1143,10 @@ __device__ __noinline__ void seq_graph(const KParams &p, Shared &sh, int32_t g, 
     int slot = 0;
     long long soff0 = nck > 0 ? issue(0, 0, b0, e0) : -1;
     for (long long k = 0; k < nck; ++k) {
-        PT_BEGIN(t_iss);
         load_rows(k + 2, b2, e2);
         const long long soff1 = k + 1 < nck ? issue(k + 1, slot ^ 1, b1, e1) : -1;
-        PT_END(p.st, 11, t_iss);
         bool staged = soff0 >= 0;
-        PT_BEGIN(t_w);
         if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = false;
-        PT_END(p.st, 9, t_w);
-        PT_BEGIN(t_pr);
         const long long cb = v0 + k * 32;
         const int32_t v = k * 32 + lane < ng ? (int32_t)(cb + lane) : -1;
         const int64_t beg = eo + b0, end = eo + e0;
@@ -1182,7 +1160,6 @@ __device__ __noinline__ void seq_graph(const KParams &p, Shared &sh, int32_t g, 
                                                        sh.warp_bm[wid], lane, dmax, ring, v0, skip_higher);
         if (push) push_lanes<BATCH>(p, sus, v, e0 - b0, g, it, lane, false);
         __syncwarp();
-        PT_END(p.st, 10, t_pr);
         b0 = b1;
         e0 = e1;
         b1 = b2;
@@ -1399,7 +1376,7 @@ __device__ __forceinline__ void chunk_of(const KParams &p, long long vc, bool vi
 // The asynchronous tentative pass resolves lanes in id order and keeps at
 // most `window` tiles in flight (window <= 0: no limit).
 template <bool ASYNC, bool BATCH>
-__device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
+__device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
                                 const int32_t *R, int32_t *W, bool push, long long &mb, int window,
                                 uint32_t &phase)
 {
@@ -1480,17 +1457,12 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
         {
             long long ncb = -1, ncend = 0;
             if (vc < nchunks) chunk_of<BATCH>(p, vc, ordered, n, ncb, ncend);
-            PT_BEGIN(t_stage);
             stage_chunk<BATCH>(p, sh, ncb, ncend, ntile, nkin, slot ^ 1, lane, wid, lim16, nxt);
-            PT_END(p.st, 0, t_stage);
         }
 
         bool staged = soff >= 0;
-        PT_BEGIN(t_wait);
         if (staged && !wait_stage(p, sh, slot, phase, wid)) staged = false;
         if (ordered && window > 0 && kin == 0 && tile >= window) wait_tile_done(p, tile - window, lane);
-        PT_END(p.st, 1, t_wait);
-        PT_BEGIN(t_proc);
         const int32_t v = cur.deg >= 0 ? (int32_t)(cb + lane) : -1;
         const int64_t end = cur.beg + (cur.deg > 0 ? cur.deg : 0);
         int32_t unclaimed = INT32_MAX;
@@ -1522,7 +1494,6 @@ __device__ GC_PASS_INLINE void implicit_staged(const KParams &p, Shared &sh, int
         }
         // Round 0 with push: the suspects form the first repair worklist.
         if (ordered && push) push_lanes<BATCH>(p, sus, v, cur.deg, cur.g, it, lane, false);
-        PT_END(p.st, ordered ? 2 : 3, t_proc);
         if (ordered && window > 0 && last_of_tile) publish_tile_done(p, tile, lane);
         __syncwarp();  // every lane is done with seg[slot] before it is refilled
         cur = nxt;
@@ -1560,10 +1531,8 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
-            PT_BEGIN(t_hub);
             bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
                      op == OP_TENT;  // round 0: hubs are kept for the first repair pass
-            PT_END(p.st, op == OP_TENT ? 4 : 12, t_hub);
             if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
                 atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
                 const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
@@ -1787,7 +1756,8 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
 // Data: p.mid_all lists the core (rank order after core_sort); while the
 // core is built, a core vertex's colour slot holds -(rank + 1); p.wl[1]
 // holds the core's adjacency as a bit matrix, word w of rank r at
-// w * H + r (column-major: the 32 ranks of a batch are one coalesced read);
+// w * Hp + r, Hp = H rounded up to a multiple of 32 (column-major: the 32
+// ranks of a batch are one coalesced read);
 // p.hub[1][r] is the first adjacency-build task of rank r (H + 1 entries).
 
 // Exclusive prefix sum over the block of one value per thread (all threads
@@ -1886,6 +1856,7 @@ __device__ __noinline__ void core_build(const KParams &p, int H, long long &mb)
     const int32_t *tpfx = p.hub[1];
     const int T = __ldcg(tpfx + H);
     uint32_t *bits = reinterpret_cast<uint32_t *>(p.wl[1]);
+    const int Hp = (H + 31) & ~31;  // column stride: word w of rank r at w * Hp + r
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&p.st->core_task, 1);
@@ -1917,26 +1888,13 @@ __device__ __noinline__ void core_build(const KParams &p, int H, long long &mb)
             for (int q = 0; q < kUnroll; ++q)
                 if (c[q] < 0) {
                     const int j = -c[q] - 1;
-                    atomicOr(bits + (size_t)(j >> 5) * H + r, 1u << (j & 31));
+                    atomicOr(bits + (size_t)(j >> 5) * Hp + r, 1u << (j & 31));
                 }
         }
         // First-Fit of a core vertex reads its row (index + colour), its row
         // pointers and writes its colour.
         if (lane == 0) mb += 8ll * (end - beg) + (k == 0 ? 12 : 0);
     }
-}
-
-// The 64 colours f, f+1, ..., f+63 of forbidden set Fl (Fw words) as a
-// mask of the free ones (bit i: colour f+i is free).
-__device__ __forceinline__ unsigned long long free_window(const uint32_t *Fl, int Fw, int f)
-{
-    const int w = f >> 5, sh = f & 31;
-    const unsigned long long a = w < Fw ? Fl[w] : 0u;
-    const unsigned long long b = w + 1 < Fw ? Fl[w + 1] : 0u;
-    const unsigned long long c = w + 2 < Fw ? Fl[w + 2] : 0u;
-    const unsigned long long lo = a | (b << 32), hi = c;
-    const unsigned long long taken = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
-    return ~taken;
 }
 
 // First colour >= 1 not in the forbidden set Fl; warp-wide (every lane
@@ -1958,79 +1916,128 @@ __device__ __forceinline__ int first_free_warp(const uint32_t *Fl, int Fw, int l
 }
 
 // Block 0: sequential First-Fit over the core in rank order, 32 ranks at a
-// time.  First every vertex of the batch collects in its forbidden set the
-// colours of its core neighbours in earlier batches (all warps; the bit
-// words of a thread are loaded together).  Then warp 0 resolves the batch
-// in rank order: a vertex takes the first colour that is neither forbidden
-// nor given to a lower-ranked neighbour of the batch.  Each lane keeps the 64
-// colours from its first free one as a register mask, and lane k's choice is
-// removed from the masks of its neighbours above it (one shuffle per rank);
-// should a mask run empty (the answer lies further up), the batch is
-// resolved again word by word.  The colours go to p.cA and, if not null, to
-// `also` (the second buffer of snapshot repairs, which only inspected
-// vertices are written to).  Returns the largest colour.
+// time.  First every vertex of the batch collects the colours of its core
+// neighbours in earlier batches (all warps; a thread's bit words are loaded
+// one batch ahead), then warp 0 resolves the batch in rank order: vertex k
+// adds the colours just given to its lower-ranked neighbours in the batch
+// and takes the first colour left.  While every colour stays below
+// kMarkColours the collected colours are byte tags in a row per vertex
+// (plain stores of the batch's tag: the warps that share a row all store the
+// same value; a warp finds the first untagged colour, 16 per lane at a
+// time), else bits in a bitset row (atomics).  The colours go to p.cA and, if not
+// null, to `also` (the second buffer of snapshot repairs, which only
+// inspected vertices are written to).  Returns the largest colour.
+// The bytes of w that differ from the tag byte (t4 = tag in all four), as
+// bits 0..3: the high bit of ((v & 0x7f..) + 0x7f..) | v is set exactly in the
+// non-zero bytes of v (no carry crosses a byte), and the multiply gathers
+// bits 7, 15, 23, 31 into bits 28..31 (the four partial products land on
+// distinct bits).
+__device__ __forceinline__ uint32_t untagged4(uint32_t w, uint32_t t4)
+{
+    const uint32_t v = w ^ t4;
+    const uint32_t nz = (((v & 0x7f7f7f7fu) + 0x7f7f7f7fu) | v) & 0x80808080u;
+    return (nz * 0x00204081u) >> 28;
+}
+
+constexpr int kMarkColours = 1024;              // colours the byte rows cover
+constexpr int kMarkStride = kMarkColours + 16;  // bytes per row (16-byte aligned, rows on different banks)
 __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int32_t *also)
 {
-    uint16_t *col16 = reinterpret_cast<uint16_t *>(&sh.seg[0][0][0]);  // colour of each rank
-    uint32_t *F = reinterpret_cast<uint32_t *>(col16 + kCoreMax);      // 32 forbidden sets of Fw words
-    const int Fw = (H + 2 + 31) / 32;                                   // colours 0..H+1
-    static_assert(sizeof(sh.seg) >= kCoreMax * 2 + 32 * ((kCoreMax + 2 + 31) / 32) * 4, "core sets fit");
+    static_assert(offsetof(Shared, ring) == sizeof(sh.seg), "staging area and ring are contiguous");
+    unsigned char *area = reinterpret_cast<unsigned char *>(&sh.seg[0][0][0]);
+    constexpr int kArea = (int)(sizeof(sh.seg) + sizeof(sh.ring));
+    uint16_t *col16 = reinterpret_cast<uint16_t *>(area);                    // colour of each rank
+    unsigned char *mark = area + kCoreMax * 2;                               // 32 byte rows
+    uint32_t *F = reinterpret_cast<uint32_t *>(area + kCoreMax * 2);         // or 32 bitset rows of Fw words
+    const int Fw = (H + 2 + 31) / 32;                                        // colours 0..H+1
+    static_assert(kCoreMax * 2 + 32 * kMarkStride <= kArea, "byte rows fit");
+    static_assert(kCoreMax * 2 + 32 * ((kCoreMax + 2 + 31) / 32) * 4 <= kArea, "bitset rows fit");
+    static_assert((kCoreMax * 2) % 16 == 0 && kMarkStride % 16 == 0, "byte rows are 16-byte aligned");
     constexpr int kWordsPerThread = (kCoreMax / 32 + kWarps - 1) / kWarps;
     const uint32_t *bits = reinterpret_cast<const uint32_t *>(p.wl[1]);
+    const int Hp = (H + 31) & ~31;  // column stride of the bit matrix
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 32 * Fw; i += kBlock) F[i] = 0u;
+    for (int i = threadIdx.x; i < 32 * kMarkStride / 4; i += kBlock) reinterpret_cast<uint32_t *>(mark)[i] = 0u;
+    bool bitset = false;  // block-uniform: colours may reach kMarkColours
     int M = 0;
+    uint32_t xs[kWordsPerThread];
+#pragma unroll
+    for (int q = 0; q < kWordsPerThread; ++q) xs[q] = 0u;  // batch 0 has no earlier batch
+    uint32_t inb = 0u;
+    int32_t vid = -1;
+    if (wid == 0 && lane < min(32, H)) {
+        inb = __ldcg(bits + lane);  // word 0 of rank lane
+        vid = __ldcg(p.mid_all + lane);
+    }
     __syncthreads();
     for (int b = 0; 32 * b < H; ++b) {
         const int nb = min(32, H - 32 * b);
+        const unsigned tag = (unsigned)b + 1;  // b < 128: one tag per batch
         if (lane < nb) {
-            const int r = 32 * b + lane;
+            unsigned char *row = mark + lane * kMarkStride;
             uint32_t *Fl = F + lane * Fw;
-            uint32_t xs[kWordsPerThread];
-#pragma unroll
-            for (int q = 0; q < kWordsPerThread; ++q) {
-                const int w = wid + q * kWarps;
-                xs[q] = w < b ? __ldcg(bits + (size_t)w * H + r) : 0u;
-            }
 #pragma unroll
             for (int q = 0; q < kWordsPerThread; ++q) {
                 uint32_t x = xs[q];
                 const int base = 32 * (wid + q * kWarps);
-                while (x) {
-                    const int c = col16[base + __ffs(x) - 1];
-                    x &= x - 1;
-                    atomicOr(Fl + (c >> 5), 1u << (c & 31));
+                if (!bitset) {
+                    while (x) {  // four bits at a time (a missing bit repeats the first)
+                        const int j0 = __ffs(x) - 1;
+                        x &= x - 1;
+                        const int j1 = x ? __ffs(x) - 1 : j0;
+                        x &= x - 1;
+                        const int j2 = x ? __ffs(x) - 1 : j0;
+                        x &= x - 1;
+                        const int j3 = x ? __ffs(x) - 1 : j0;
+                        x &= x - 1;
+                        const int c0 = col16[base + j0], c1 = col16[base + j1];
+                        const int c2 = col16[base + j2], c3 = col16[base + j3];
+                        row[c0] = (unsigned char)tag;
+                        row[c1] = (unsigned char)tag;
+                        row[c2] = (unsigned char)tag;
+                        row[c3] = (unsigned char)tag;
+                    }
+                } else {
+                    while (x) {
+                        const int c = col16[base + __ffs(x) - 1];
+                        x &= x - 1;
+                        atomicOr(Fl + (c >> 5), 1u << (c & 31));
+                    }
                 }
             }
         }
+        // the next batch's words (they do not depend on colours)
+        const int b1 = b + 1, r1 = 32 * b1 + lane;
+#pragma unroll
+        for (int q = 0; q < kWordsPerThread; ++q) {
+            const int w = wid + q * kWarps;
+            xs[q] = (w < b1 && r1 < H) ? __ldcg(bits + (size_t)w * Hp + r1) : 0u;
+        }
         __syncthreads();
         if (wid == 0) {
-            const uint32_t inb = lane < nb ? __ldcg(bits + (size_t)b * H + 32 * b + lane) : 0u;
-            const uint32_t *Fl = F + lane * Fw;
-            // first free colour of each lane's set, then its 64-colour window
-            int f = 1;
-            if (lane < nb) {
-                int w = 0;
-                uint32_t fr = ~Fl[0] & ~1u;
-                while (fr == 0u && w + 1 < Fw) fr = ~Fl[++w];
-                f = w * 32 + __ffs(fr) - 1;
-            }
-            unsigned long long m = lane < nb ? free_window(Fl, Fw, f) : 1ull;
             int mine = 0;
-            bool empty = false;
-            for (int k = 0; k < nb; ++k) {
-                const int cand = m ? f + __ffsll((long long)m) - 1 : 0;
-                const int ck = __shfl_sync(FULL_MASK, cand, k);
-                if (lane == k) {
-                    mine = ck;
-                    empty = (m == 0ull);
+            if (!bitset) {
+                const uint32_t t4 = tag * 0x01010101u;
+                for (int k = 0; k < nb; ++k) {
+                    unsigned char *rowk = mark + k * kMarkStride;
+                    if (lane < k && ((inb >> k) & 1u)) rowk[mine] = (unsigned char)tag;
+                    __syncwarp();
+                    int c = 0;
+                    for (int c0 = 0; c == 0 && c0 < kMarkColours; c0 += 512) {  // colours c0 + 16*lane .. +15
+                        const uint4 w4 = *reinterpret_cast<const uint4 *>(rowk + c0 + 16 * lane);
+                        uint32_t fm = untagged4(w4.x, t4) | (untagged4(w4.y, t4) << 4) | (untagged4(w4.z, t4) << 8) |
+                                      (untagged4(w4.w, t4) << 12);  // bit i: colour c0 + 16*lane + i untagged
+                        if (c0 == 0 && lane == 0) fm &= ~1u;  // colour 0 is not a colour
+                        const unsigned bal = __ballot_sync(FULL_MASK, fm != 0u);
+                        if (bal) {
+                            const int src = __ffs(bal) - 1;
+                            const uint32_t fb = __shfl_sync(FULL_MASK, fm, src);
+                            c = c0 + 16 * src + __ffs(fb) - 1;
+                        }
+                    }
+                    if (lane == k) mine = c;
                 }
-                const unsigned d = (unsigned)(ck - f);
-                if (lane > k && ((inb >> k) & 1u) && d < 64u) m &= ~(1ull << d);
-            }
-            if (__any_sync(FULL_MASK, empty)) {
-                // exact fallback: word-by-word search in rank order
-                mine = 0;
+            } else {
                 for (int k = 0; k < nb; ++k) {
                     if (lane < k && ((inb >> k) & 1u)) atomicOr(F + k * Fw + (mine >> 5), 1u << (mine & 31));
                     __syncwarp();
@@ -2040,18 +2047,27 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
             }
             if (lane < nb) {
                 col16[32 * b + lane] = (uint16_t)mine;
-                const int32_t v = __ldcg(p.mid_all + 32 * b + lane);
-                st_color<true>(p.cA + v, mine);
-                if (also) st_color<true>(also + v, mine);
+                st_color<true>(p.cA + vid, mine);
+                if (also) st_color<true>(also + vid, mine);
             }
             const int bm = __reduce_max_sync(FULL_MASK, mine);
+            // the next batch's in-batch word and vertices
+            inb = r1 < H ? __ldcg(bits + (size_t)b1 * Hp + r1) : 0u;
+            vid = r1 < H ? __ldcg(p.mid_all + r1) : -1;
             if (lane == 0) sh.claim = max(M, bm);
         }
         __syncthreads();
+        const int Mprev = M;
         M = sh.claim;
-        // every set bit of the forbidden sets is a colour <= M: clear those words
-        const int fw = min(Fw, (M >> 5) + 1);
-        for (int i = threadIdx.x; i < 32 * fw; i += kBlock) F[(i / fw) * Fw + (i % fw)] = 0u;
+        if (!bitset && M + 32 >= kMarkColours) {
+            // the next batch could reach kMarkColours: bitset rows from here on
+            bitset = true;
+            for (int i = threadIdx.x; i < 32 * Fw; i += kBlock) F[i] = 0u;
+        } else if (bitset) {
+            // every set bit is a colour <= M: clear those words
+            const int fw = min(Fw, (max(M, Mprev) >> 5) + 1);
+            for (int i = threadIdx.x; i < 32 * fw; i += kBlock) F[(i / fw) * Fw + (i % fw)] = 0u;
+        }
         __syncthreads();
     }
     return M;
@@ -2059,7 +2075,7 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
 
 
 template <bool ASYNC, bool BATCH>
-__global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
+__global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
 {
     extern __shared__ __align__(128) unsigned char gc_smem[];
     Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
@@ -2089,7 +2105,6 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // Deterministic round 0 colours every vertex from a snapshot in which
         // nothing is coloured yet, so every vertex gets colour 1.
         const long long stride = (long long)gridDim.x * kBlock;
-        PT_BEGIN(t_pro);
         if (recolor && (!ASYNC || keep)) {
             // Incremental recolouring needs no binning (no round 0): only the
             // second snapshot buffer or the keepers marks are initialised.
@@ -2101,7 +2116,6 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
         // Four vertices per thread per step, their row lookups issued together
         // (each is a chain of dependent loads in a batch).
         constexpr int kProU = 4;
-        PT_BEGIN(t_bin);
         for (long long b0 = (long long)blockIdx.x * kBlock; b0 < (recolor ? 0ll : (long long)p.n);
              b0 += kProU * stride) {
             int64_t degs[kProU];
@@ -2210,7 +2224,6 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 }
             }
         }
-        PT_END(p.st, 15, t_bin);
         if (BATCH && p.g_rounds)
             for (long long g = (long long)blockIdx.x * kBlock + threadIdx.x; g < p.G; g += stride)
                 p.g_rounds[g] = (__ldg(p.vtx_off + g + 1) > __ldg(p.vtx_off + g)) ? 1 : 0;
@@ -2263,7 +2276,6 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
                 }
             }
         }
-        PT_END(p.st, 14, t_pro);
         if (recolor)  // repeat filter of the touched list
             for (long long w = (long long)blockIdx.x * kBlock + threadIdx.x; w < (long long)p.n / 32 + 1; w += stride)
                 p.done[w] = 0;
@@ -2311,11 +2323,11 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             if (!BATCH && p.core_deg > 0) {
                 const int H = ld_volatile(&st->core_count);
                 const int W = (H + 31) / 32;
-                if (H > 0 && H <= kCoreMax && (long long)H * W <= (long long)p.n) {
+                if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
                     core_n = H;
                     if (blockIdx.x == 0) core_sort(p, sh, H);
                     if (nbl == 1 || blockIdx.x > 0) {
-                        const long long words = (long long)H * W;
+                        const long long words = (long long)32 * W * W;
                         const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
                         const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
                         for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
@@ -2382,9 +2394,7 @@ __global__ void __launch_bounds__(kBlock, GC_MIN_BLOCKS) color_kernel(KParams p)
             // those (every other vertex of U^0 = V is provably clean).
             if (ASYNC && !twop && !recolor) {
                 const bool suspects = !snap;
-                PT_BEGIN(t_r0);
                 run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, window);
-                PT_END(p.st, 13, t_r0);
                 grid_sync(st, nbl);
                 if (blockIdx.x == 0 && threadIdx.x == 0 && it < kStamps) st->stamp[it] = global_timer();
                 if (ld_volatile(&st->error)) {

@@ -26,6 +26,7 @@
 #include "gc.h"
 #include "gc_ctx.h"
 #include "gc_internal.h"
+#include "gc_nvtx.h"
 
 namespace {
 
@@ -106,6 +107,7 @@ bool device_accessible(const void *p)
 extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, const gc_opts *opts,
                                 int32_t *colors_out, gc_stats *stats_out, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_color_noalloc");
     if (!csr || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
     if (!gc::dist1_mode_ok(mode)) return GC_ERR_ARG;
     if (n > kMaxN) return GC_ERR_TOO_LARGE;

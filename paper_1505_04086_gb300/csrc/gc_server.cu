@@ -2,11 +2,14 @@
 //
 // Requests (host CSR graphs) are copied into a pinned host pool at submit
 // time.  A worker thread admits them in arrival order into a fixed device
-// arena (the memory budget), uploading on a copy stream, and whenever the
-// GPU is free it colours every uploaded request in one batched persistent
-// launch (a "wave"): requests that arrive while a wave runs are uploaded
-// meanwhile and join the next wave.  Results are copied back to the pinned
-// pool and handed out by gc_server_poll / gc_server_wait.
+// arena (the memory budget), uploading on a copy stream, and colours every
+// uploaded request in one batched persistent launch (a "wave") on one of
+// kLanes compute lanes (stream + context + wave buffers).  A wave starts as
+// soon as a lane is free and a request is uploaded: requests that arrive
+// while a wave runs go into the next wave, which runs on the other lane
+// beside it, each wave's grid sized to its share of the SMs.  Results are
+// copied back to the pinned pool and handed out by gc_server_poll /
+// gc_server_wait; gc_server_cancel drops a request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,7 +25,9 @@
 #include <vector>
 
 #include "gc.h"
+#include "gc_ctx.h"
 #include "gc_internal.h"
+#include "gc_nvtx.h"
 
 namespace {
 
@@ -92,6 +97,32 @@ struct Request {
     Clock::time_point t_submit, t_done;
     int32_t *h_rp = nullptr, *h_ci = nullptr, *h_col = nullptr;
     unsigned char *own_pinned = nullptr;  // host block of its own when the pool was full
+    bool cancelled = false;               // ticket released; dropped when its GPU work ends
+};
+
+constexpr int kLanes = 2;      // waves that can be on the GPU at once
+constexpr int kHistory = 64;   // completed wave intervals kept for the overlap count
+
+// One compute lane: a stream, a context (scratch), the wave tables and
+// colours, and the wave it runs.
+struct Lane {
+    gc_ctx *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t *h_tab = nullptr;  // vtx_off[G+1] | edge_off[G+1] | rp_off[G+1] (pinned)
+    int64_t *d_tab = nullptr;
+    int32_t *d_rounds = nullptr, *h_rounds = nullptr;
+    int64_t *d_confl = nullptr, *h_confl = nullptr;
+    int32_t *d_colors = nullptr;
+    int64_t colors_cap = 0;
+    cudaEvent_t done = nullptr;                   // wave finished (results on the host)
+    cudaEvent_t t_start = nullptr, t_end = nullptr;  // timing: around the colouring
+    std::vector<Request *> wave;
+    bool inflight = false;
+};
+
+struct Interval {
+    int lane;
+    float start_ms, end_ms;  // since the server's epoch event
 };
 
 int64_t dev_footprint(int32_t n, int64_t nnz) { return ((int64_t)n + 1 + nnz) * 4; }
@@ -105,24 +136,16 @@ struct gc_server {
     gc_opts opts;
     bool have_opts = false;
     int max_slots = 0;
-    gc_ctx *ctx = nullptr;
-    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaStream_t copy = nullptr;
     // device arena (the budget) and pinned host pool
     unsigned char *arena = nullptr;
     Arena arena_alloc;
     unsigned char *pinned = nullptr;
     Arena pinned_alloc;
-    // wave tables: pinned staging + device copies, capacity max_slots
-    int64_t *h_tab = nullptr;   // vtx_off[G+1] | edge_off[G+1] | rp_off[G+1]
-    int64_t *d_tab = nullptr;
-    int32_t *d_rounds = nullptr, *h_rounds = nullptr;
-    int64_t *d_confl = nullptr, *h_confl = nullptr;
-    int32_t *d_colors = nullptr;  // wave colours
-    int64_t colors_cap = 0;
-    cudaEvent_t wave_done = nullptr;
-    std::vector<Request *> wave;
-    bool wave_inflight = false;
-    Clock::time_point wave_start;
+    Lane lanes[kLanes];
+    cudaEvent_t epoch = nullptr;  // timing origin of the wave intervals
+    Interval history[kHistory];
+    int nhistory = 0;
     // queues and bookkeeping
     std::mutex mu;
     std::condition_variable cv_done, cv_work;
@@ -165,39 +188,80 @@ void release_device(gc_server *s, Request *r)
     }
 }
 
+void destroy_request(gc_server *s, Request *r);
+
 void finish(gc_server *s, Request *r, int status)
 {
     r->status = status;
     r->state = DONE;
     r->t_done = Clock::now();
     release_device(s, r);
+    if (r->cancelled) {  // nobody will poll it
+        destroy_request(s, r);
+        return;
+    }
     if (status == GC_OK || status == GC_ERR_NO_CONVERGENCE) s->info.completed++;
     else s->info.failed++;
 }
 
-// Complete the running wave (its event has fired).
-void complete_wave(gc_server *s)
+// The GPU interval of a completed wave (event timestamps, ms since the
+// epoch): add its overlap with the earlier completed waves of other lanes.
+void account_overlap(gc_server *s, int lane)
 {
+    const Lane &L = s->lanes[lane];
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, s->epoch, L.t_start) != cudaSuccess ||
+        cudaEventElapsedTime(&b, s->epoch, L.t_end) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    bool overlapped = false;
+    const int k = std::min(s->nhistory, kHistory);
+    for (int i = 0; i < k; ++i) {
+        const Interval &h = s->history[i];
+        if (h.lane == lane) continue;
+        const float ov = std::min(b, h.end_ms) - std::max(a, h.start_ms);
+        if (ov > 0.f) {
+            s->info.overlap_us += (int64_t)(ov * 1000.f);
+            overlapped = true;
+        }
+    }
+    if (overlapped) s->info.overlapped_waves++;
+    s->history[s->nhistory % kHistory] = Interval{lane, a, b};
+    s->nhistory++;
+}
+
+// Complete the wave of a lane (its event has fired).
+void complete_wave(gc_server *s, int lane)
+{
+    Lane &L = s->lanes[lane];
     gc_stats st;
     memset(&st, 0, sizeof st);
-    const int rc = gc_ctx_stats(s->ctx, &st);
-    for (size_t g = 0; g < s->wave.size(); ++g) {
-        Request *r = s->wave[g];
-        r->rounds = s->h_rounds[g];
-        r->conflicts = s->h_confl[g];
+    const int rc = gc_ctx_stats(L.ctx, &st);
+    account_overlap(s, lane);
+    for (size_t g = 0; g < L.wave.size(); ++g) {
+        Request *r = L.wave[g];
+        r->rounds = L.h_rounds[g];
+        r->conflicts = L.h_confl[g];
         finish(s, r, rc);
     }
-    s->wave.clear();
-    s->wave_inflight = false;
+    L.wave.clear();
+    L.inflight = false;
     s->cv_done.notify_all();
+}
+
+int resident_count(const gc_server *s)
+{
+    int k = (int)s->uploading.size();
+    for (const Lane &L : s->lanes) k += (int)L.wave.size();
+    return k;
 }
 
 // Admit queued requests (in order) while arena space and slots allow.
 bool admit(gc_server *s)
 {
     bool any = false;
-    const int resident = (int)(s->uploading.size() + s->wave.size());
-    int room = s->max_slots - resident;
+    int room = s->max_slots - resident_count(s);
     while (!s->queue.empty() && room > 0) {
         Request *r = s->queue.front();
         const int64_t off = s->arena_alloc.alloc(r->dev_bytes);
@@ -225,37 +289,46 @@ bool admit(gc_server *s)
     return any;
 }
 
-bool ensure_wave_colors(gc_server *s, int64_t n)
+bool ensure_wave_colors(Lane &L, int64_t n)
 {
-    if (n <= s->colors_cap) return true;
-    if (s->d_colors) cudaFree(s->d_colors);
-    s->d_colors = nullptr;
-    s->colors_cap = 0;
+    if (n <= L.colors_cap) return true;
+    if (L.d_colors) cudaFree(L.d_colors);
+    L.d_colors = nullptr;
+    L.colors_cap = 0;
     const int64_t cap = std::max<int64_t>(n, 1 << 20);
-    if (cudaMalloc(&s->d_colors, (size_t)cap * 4) != cudaSuccess) {
+    if (cudaMalloc(&L.d_colors, (size_t)cap * 4) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    s->colors_cap = cap;
+    L.colors_cap = cap;
     return true;
 }
 
-// Launch one wave over every request whose upload has completed.
-bool launch_wave(gc_server *s)
+// Launch one wave on an idle lane over every request whose upload has
+// completed (cancelled ones are dropped here).
+bool launch_wave(gc_server *s, int lane)
 {
+    Lane &L = s->lanes[lane];
     std::vector<Request *> ready, waiting;
+    bool dropped = false;
     for (Request *r : s->uploading) {
         const cudaError_t q = cudaEventQuery(r->uploaded);
-        if (q == cudaSuccess) ready.push_back(r);
-        else {
+        if (q == cudaSuccess) {
+            if (r->cancelled) {
+                destroy_request(s, r);
+                dropped = true;
+            } else {
+                ready.push_back(r);
+            }
+        } else {
             if (q != cudaErrorNotReady) cudaGetLastError();
             waiting.push_back(r);
         }
     }
-    if (ready.empty()) return false;
     s->uploading = waiting;
+    if (ready.empty()) return dropped;
     const int G = (int)ready.size();
-    int64_t *vtx = s->h_tab, *edge = s->h_tab + (G + 1), *rpo = s->h_tab + 2 * (G + 1);
+    int64_t *vtx = L.h_tab, *edge = L.h_tab + (G + 1), *rpo = L.h_tab + 2 * (G + 1);
     vtx[0] = 0;
     for (int g = 0; g < G; ++g) {
         Request *r = ready[g];
@@ -268,27 +341,28 @@ bool launch_wave(gc_server *s)
     rpo[G] = 0;
     const int64_t total_n = vtx[G];
     int rc = GC_OK;
-    if (!ensure_wave_colors(s, total_n)) rc = GC_ERR_OOM;
+    if (!ensure_wave_colors(L, total_n)) rc = GC_ERR_OOM;
     cudaError_t e = cudaSuccess;
     if (rc == GC_OK)
-        e = cudaMemcpyAsync(s->d_tab, s->h_tab, (size_t)3 * (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
-                            s->compute);
+        e = cudaMemcpyAsync(L.d_tab, L.h_tab, (size_t)3 * (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            L.stream);
+    if (rc == GC_OK && e == cudaSuccess) e = cudaEventRecord(L.t_start, L.stream);
     if (rc == GC_OK && e == cudaSuccess)
-        rc = gc::color_batch_offsets(s->ctx, G, total_n, s->arena_alloc.size() / 4, s->d_tab, s->d_tab + (G + 1),
-                                     s->d_tab + 2 * (G + 1), reinterpret_cast<const int32_t *>(s->arena), s->mode,
-                                     s->have_opts ? &s->opts : nullptr, s->d_colors, s->d_rounds, s->d_confl,
-                                     s->compute);
+        rc = gc::color_batch_offsets(L.ctx, G, total_n, s->arena_alloc.size() / 4, L.d_tab, L.d_tab + (G + 1),
+                                     L.d_tab + 2 * (G + 1), reinterpret_cast<const int32_t *>(s->arena), s->mode,
+                                     &s->opts, L.d_colors, L.d_rounds, L.d_confl, L.stream);
+    if (rc == GC_OK && e == cudaSuccess) e = cudaEventRecord(L.t_end, L.stream);
     if (e != cudaSuccess) rc = GC_ERR_CUDA;
     for (int g = 0; g < G && rc == GC_OK; ++g) {
         Request *r = ready[g];
-        if (r->n > 0 && cudaMemcpyAsync(r->h_col, s->d_colors + vtx[g], (size_t)r->n * 4, cudaMemcpyDeviceToHost,
-                                        s->compute) != cudaSuccess)
+        if (r->n > 0 && cudaMemcpyAsync(r->h_col, L.d_colors + vtx[g], (size_t)r->n * 4, cudaMemcpyDeviceToHost,
+                                        L.stream) != cudaSuccess)
             rc = GC_ERR_CUDA;
     }
     if (rc == GC_OK &&
-        (cudaMemcpyAsync(s->h_rounds, s->d_rounds, (size_t)G * 4, cudaMemcpyDeviceToHost, s->compute) != cudaSuccess ||
-         cudaMemcpyAsync(s->h_confl, s->d_confl, (size_t)G * 8, cudaMemcpyDeviceToHost, s->compute) != cudaSuccess ||
-         cudaEventRecord(s->wave_done, s->compute) != cudaSuccess))
+        (cudaMemcpyAsync(L.h_rounds, L.d_rounds, (size_t)G * 4, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess ||
+         cudaMemcpyAsync(L.h_confl, L.d_confl, (size_t)G * 8, cudaMemcpyDeviceToHost, L.stream) != cudaSuccess ||
+         cudaEventRecord(L.done, L.stream) != cudaSuccess))
         rc = GC_ERR_CUDA;
     if (rc != GC_OK) {
         cudaGetLastError();
@@ -297,9 +371,8 @@ bool launch_wave(gc_server *s)
         return true;
     }
     for (Request *r : ready) r->state = IN_WAVE;
-    s->wave = ready;
-    s->wave_inflight = true;
-    s->wave_start = Clock::now();
+    L.wave = ready;
+    L.inflight = true;
     s->info.waves++;
     s->info.max_wave_graphs = std::max<int32_t>(s->info.max_wave_graphs, G);
     return true;
@@ -311,21 +384,25 @@ void worker_main(gc_server *s)
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
         bool progress = false;
-        if (s->wave_inflight) {
-            const cudaError_t q = cudaEventQuery(s->wave_done);
+        for (int l = 0; l < kLanes; ++l) {
+            Lane &L = s->lanes[l];
+            if (!L.inflight) continue;
+            const cudaError_t q = cudaEventQuery(L.done);
             if (q == cudaSuccess) {
-                complete_wave(s);
+                complete_wave(s, l);
                 progress = true;
             } else if (q != cudaErrorNotReady) {
                 cudaGetLastError();
-                complete_wave(s);
+                complete_wave(s, l);
                 progress = true;
             }
         }
         if (admit(s)) progress = true;
-        if (!s->wave_inflight && launch_wave(s)) progress = true;
+        for (int l = 0; l < kLanes && !s->uploading.empty(); ++l)
+            if (!s->lanes[l].inflight && launch_wave(s, l)) progress = true;
         if (!progress) {
-            const bool busy = s->wave_inflight || !s->uploading.empty();
+            bool busy = !s->uploading.empty();
+            for (const Lane &L : s->lanes) busy = busy || L.inflight;
             if (busy) {
                 lk.unlock();
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -394,28 +471,35 @@ int gc_server_create(gc_server **out, int device, size_t budget, int max_slots, 
     s->device = device;
     s->mode = mode | GC_NO_COLOR_STATS;  // per-request colour counts are taken on the host
     s->max_slots = max_slots;
-    if (opts) {
-        s->opts = *opts;
-        s->have_opts = true;
-    }
-    int rc = gc_ctx_create(&s->ctx, device);
+    memset(&s->opts, 0, sizeof s->opts);
+    if (opts) s->opts = *opts;
+    int rc = GC_OK;
+    for (int l = 0; l < kLanes && rc == GC_OK; ++l) rc = gc_ctx_create(&s->lanes[l].ctx, device);
     int prev = 0;
     cudaGetDevice(&prev);
     cudaError_t e = cudaSuccess;
     if (rc == GC_OK) {
         e = cudaSetDevice(device);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&s->arena, budget);
         if (e == cudaSuccess) e = cudaMallocHost(&s->pinned, 2 * budget);
+        if (e == cudaSuccess) e = cudaEventCreate(&s->epoch);
         const size_t tab = (size_t)3 * (max_slots + 1) * sizeof(int64_t);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->h_tab, tab);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_tab, tab);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_rounds, (size_t)max_slots * 4);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->h_rounds, (size_t)max_slots * 4);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_confl, (size_t)max_slots * 8);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->h_confl, (size_t)max_slots * 8);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->wave_done, cudaEventDisableTiming);
+        for (int l = 0; l < kLanes && e == cudaSuccess; ++l) {
+            Lane &L = s->lanes[l];
+            e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaMallocHost(&L.h_tab, tab);
+            if (e == cudaSuccess) e = cudaMalloc(&L.d_tab, tab);
+            if (e == cudaSuccess) e = cudaMalloc(&L.d_rounds, (size_t)max_slots * 4);
+            if (e == cudaSuccess) e = cudaMallocHost(&L.h_rounds, (size_t)max_slots * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&L.d_confl, (size_t)max_slots * 8);
+            if (e == cudaSuccess) e = cudaMallocHost(&L.h_confl, (size_t)max_slots * 8);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreate(&L.t_start);
+            if (e == cudaSuccess) e = cudaEventCreate(&L.t_end);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(s->epoch, s->copy);
+        if (e == cudaSuccess) e = cudaEventSynchronize(s->epoch);
         if (e != cudaSuccess) {
             cudaGetLastError();
             rc = e == cudaErrorMemoryAllocation ? GC_ERR_OOM : GC_ERR_CUDA;
@@ -426,9 +510,16 @@ int gc_server_create(gc_server **out, int device, size_t budget, int max_slots, 
         gc_server_destroy(s);
         return rc;
     }
+    // Each wave takes its share of the SMs, so that the waves of the lanes
+    // run side by side (unless the caller chose the blocks per SM).
+    if (s->opts.blocks_per_sm == 0) {
+        const bool async = (mode & GC_SCHED_ASYNC) != 0;
+        s->opts.blocks_per_sm = std::max(1, s->lanes[0].ctx->occ[async][1] / kLanes);
+    }
     s->arena_alloc.reset((int64_t)budget);
     s->pinned_alloc.reset((int64_t)(2 * budget));
     s->info.budget_bytes = (int64_t)budget;
+    s->info.lanes = kLanes;
     s->worker = std::thread(worker_main, s);
     *out = s;
     return GC_OK;
@@ -436,6 +527,7 @@ int gc_server_create(gc_server **out, int device, size_t budget, int max_slots, 
 
 int gc_server_submit(gc_server *s, const gc_csr *csr, int32_t n, int64_t nnz, uint64_t *ticket)
 {
+    gc::NvtxRange nvtx_range("gc_server_submit");
     if (!s || !csr || !ticket || n < 0 || nnz < 0 || nnz > INT32_MAX) return GC_ERR_ARG;
     if (n > 0 && !csr->row_ptr) return GC_ERR_ARG;
     if (nnz > 0 && !csr->col_idx) return GC_ERR_ARG;
@@ -510,6 +602,7 @@ int gc_server_poll(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats 
 
 int gc_server_wait(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats *stats_out, int32_t timeout_ms)
 {
+    gc::NvtxRange nvtx_range("gc_server_wait");
     if (!s) return GC_ERR_ARG;
     {
         std::unique_lock<std::mutex> lk(s->mu);
@@ -525,6 +618,27 @@ int gc_server_wait(gc_server *s, uint64_t ticket, int32_t *colors_out, gc_stats 
     return gc_server_poll(s, ticket, colors_out, stats_out);
 }
 
+int gc_server_cancel(gc_server *s, uint64_t ticket)
+{
+    if (!s) return GC_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return GC_ERR_NOT_FOUND;
+    Request *r = it->second;
+    s->all.erase(it);
+    s->info.cancelled++;
+    if (r->state == QUEUED) {
+        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
+        destroy_request(s, r);
+    } else if (r->state == DONE) {
+        destroy_request(s, r);
+    } else {
+        r->cancelled = true;  // on the GPU: dropped when its upload or wave ends
+    }
+    s->cv_done.notify_all();
+    return GC_OK;
+}
+
 int gc_server_query(gc_server *s, gc_server_info *out)
 {
     if (!s || !out) return GC_ERR_ARG;
@@ -532,7 +646,7 @@ int gc_server_query(gc_server *s, gc_server_info *out)
     *out = s->info;
     out->in_use_bytes = s->arena_alloc.used();
     out->queued = (int32_t)s->queue.size();
-    out->resident = (int32_t)(s->uploading.size() + s->wave.size());
+    out->resident = (int32_t)resident_count(s);
     return GC_OK;
 }
 
@@ -548,8 +662,15 @@ void gc_server_destroy(gc_server *s)
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
-    if (s->compute) cudaStreamSynchronize(s->compute);
     if (s->copy) cudaStreamSynchronize(s->copy);
+    for (Lane &L : s->lanes)
+        if (L.stream) cudaStreamSynchronize(L.stream);
+    // cancelled requests still held by the worker's lists, then the rest
+    for (Request *r : s->uploading)
+        if (r->cancelled) destroy_request(s, r);
+    for (Lane &L : s->lanes)
+        for (Request *r : L.wave)
+            if (r->cancelled) destroy_request(s, r);
     for (auto &kv : s->all) {
         release_device(s, kv.second);
         if (kv.second->own_pinned) cudaFreeHost(kv.second->own_pinned);
@@ -557,18 +678,23 @@ void gc_server_destroy(gc_server *s)
     }
     s->all.clear();
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
-    if (s->wave_done) cudaEventDestroy(s->wave_done);
-    if (s->ctx) gc_ctx_destroy(s->ctx);
+    for (Lane &L : s->lanes) {
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.t_start) cudaEventDestroy(L.t_start);
+        if (L.t_end) cudaEventDestroy(L.t_end);
+        if (L.ctx) gc_ctx_destroy(L.ctx);
+        if (L.h_tab) cudaFreeHost(L.h_tab);
+        if (L.d_tab) cudaFree(L.d_tab);
+        if (L.d_rounds) cudaFree(L.d_rounds);
+        if (L.h_rounds) cudaFreeHost(L.h_rounds);
+        if (L.d_confl) cudaFree(L.d_confl);
+        if (L.h_confl) cudaFreeHost(L.h_confl);
+        if (L.d_colors) cudaFree(L.d_colors);
+        if (L.stream) cudaStreamDestroy(L.stream);
+    }
+    if (s->epoch) cudaEventDestroy(s->epoch);
     if (s->arena) cudaFree(s->arena);
     if (s->pinned) cudaFreeHost(s->pinned);
-    if (s->h_tab) cudaFreeHost(s->h_tab);
-    if (s->d_tab) cudaFree(s->d_tab);
-    if (s->d_rounds) cudaFree(s->d_rounds);
-    if (s->h_rounds) cudaFreeHost(s->h_rounds);
-    if (s->d_confl) cudaFree(s->d_confl);
-    if (s->h_confl) cudaFreeHost(s->h_confl);
-    if (s->d_colors) cudaFree(s->d_colors);
-    if (s->compute) cudaStreamDestroy(s->compute);
     if (s->copy) cudaStreamDestroy(s->copy);
     cudaGetLastError();
     cudaSetDevice(prev);

@@ -4,14 +4,19 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include <utility>
 #include <vector>
 
 #include "gc.h"
 #include "gc_ctx.h"
 #include "gc_internal.h"
+#include "gc_nvtx.h"
 
 struct gc_plan {
     gc_ctx *ctx = nullptr;               // private: its scratch never moves under the graph
@@ -45,6 +50,74 @@ int run_batch(gc_ctx *c, const gc_batch *b, uint32_t mode, const gc_opts *o, int
 {
     return gc::color_batch_impl(c, b->G, b->total_n, b->total_nnz, b->vtx_off, b->edge_off, nullptr, b->row_ptr,
                                 b->col_idx, mode, o, colors_out, nullptr, nullptr, s);
+}
+
+// On-disk cache of tuning results, used when the environment variable
+// GC_TUNE_CACHE names a file: one text line per tuned problem,
+//   <key> t1 t2 tile blocks_per_sm tail window best_ms default_ms
+// where the key names the library version, the call (one graph or a batch),
+// the mode, the graph's shape (vertices, entries, graphs), the SM count and
+// the repetitions.  Lines are appended; the last line of a key wins.
+std::mutex g_cache_mu;
+
+std::string cache_key(const char *kind, uint32_t mode, int64_t n, int64_t nnz, int64_t G, int sms, int reps)
+{
+    char buf[192];
+    snprintf(buf, sizeof buf, "gc%d:%s:mode=%u:n=%lld:nnz=%lld:G=%lld:sms=%d:reps=%d", gc_version(), kind, mode,
+             (long long)n, (long long)nnz, (long long)G, sms, reps);
+    return buf;
+}
+
+bool cache_lookup(const std::string &key, gc_tune_result *out)
+{
+    const char *path = getenv("GC_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool hit = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[256];
+        gc_opts o;
+        memset(&o, 0, sizeof o);
+        float best = 0.f, def = 0.f;
+        if (sscanf(line, "%255s %d %d %d %d %d %d %f %f", k, &o.t1, &o.t2, &o.tile, &o.blocks_per_sm, &o.tail,
+                   &o.window, &best, &def) != 9 || key != k)
+            continue;
+        out->best = o;
+        out->best_ms = best;
+        out->default_ms = def;
+        hit = true;
+    }
+    fclose(f);
+    return hit;
+}
+
+void cache_store(const std::string &key, const gc_tune_result &r)
+{
+    const char *path = getenv("GC_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %d %.6f %.6f\n", key.c_str(), r.best.t1, r.best.t2, r.best.tile,
+            r.best.blocks_per_sm, r.best.tail, r.best.window, r.best_ms, r.default_ms);
+    fclose(f);
+}
+
+// A cached result: one colouring with its options (colors_out receives it);
+// evaluated = 0 tells the caller nothing was searched.
+template <class Run>
+int from_cache(gc_ctx *ctx, const std::string &key, gc_tune_result *out, Run run)
+{
+    memset(out, 0, sizeof *out);
+    if (!cache_lookup(key, out)) return GC_ERR_NOT_FOUND;
+    int rc = run(out->best);
+    gc_stats st;
+    memset(&st, 0, sizeof st);
+    if (rc == GC_OK) rc = gc_ctx_stats(ctx, &st);
+    return rc;
 }
 
 // Coordinate descent over the option knobs (see gc_autotune_batch in gc.h):
@@ -143,6 +216,7 @@ extern "C" {
 int gc_plan_create(const gc_batch *b, int device, uint32_t mode, const gc_opts *opts, int32_t *colors_out,
                    int32_t *rounds_out, int64_t *conflicts_out, gc_plan **out)
 {
+    gc::NvtxRange nvtx_range("gc_plan_create");
     if (!out) return GC_ERR_ARG;
     *out = nullptr;
     if (!batch_ok(b) || !gc::dist1_mode_ok(mode) || (b->total_n > 0 && !colors_out)) return GC_ERR_ARG;
@@ -180,6 +254,7 @@ int gc_plan_create(const gc_batch *b, int device, uint32_t mode, const gc_opts *
 
 int gc_plan_launch(gc_plan *pl, void *stream)
 {
+    gc::NvtxRange nvtx_range("gc_plan_launch");
     if (!pl || !pl->exec) return GC_ERR_ARG;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -226,21 +301,33 @@ void gc_plan_destroy(gc_plan *pl)
 int gc_autotune_batch(gc_ctx *ctx, const gc_batch *b, uint32_t mode, int32_t reps, int32_t *colors_out,
                       gc_tune_result *out)
 {
+    gc::NvtxRange nvtx_range("gc_autotune_batch");
     if (!ctx || !out || !batch_ok(b) || !gc::dist1_mode_ok(mode) || (b->total_n > 0 && !colors_out) || reps < 1 ||
         reps > 64)
         return GC_ERR_ARG;
-    return tune(ctx, reps, mode, out,
-                [&](const gc_opts &o) { return run_batch(ctx, b, mode, &o, colors_out, nullptr); });
+    auto run = [&](const gc_opts &o) { return run_batch(ctx, b, mode, &o, colors_out, nullptr); };
+    const std::string key = cache_key("batch", mode, b->total_n, b->total_nnz, b->G, ctx->num_sms, reps);
+    int rc = from_cache(ctx, key, out, run);
+    if (rc != GC_ERR_NOT_FOUND) return rc;
+    rc = tune(ctx, reps, mode, out, run);
+    if (rc == GC_OK) cache_store(key, *out);
+    return rc;
 }
 
 int gc_autotune(gc_ctx *ctx, const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t reps,
                 int32_t *colors_out, gc_tune_result *out)
 {
+    gc::NvtxRange nvtx_range("gc_autotune");
     if (!ctx || !out || !csr || n < 0 || nnz < 0 || nnz > INT32_MAX || !gc::dist1_mode_ok(mode) ||
         (n > 0 && (!csr->row_ptr || !colors_out)) || (nnz > 0 && !csr->col_idx) || reps < 1 || reps > 64)
         return GC_ERR_ARG;
-    return tune(ctx, reps, mode, out,
-                [&](const gc_opts &o) { return gc_color_async(ctx, csr, n, nnz, mode, &o, colors_out, nullptr); });
+    auto run = [&](const gc_opts &o) { return gc_color_async(ctx, csr, n, nnz, mode, &o, colors_out, nullptr); };
+    const std::string key = cache_key("graph", mode, n, nnz, 1, ctx->num_sms, reps);
+    int rc = from_cache(ctx, key, out, run);
+    if (rc != GC_ERR_NOT_FOUND) return rc;
+    rc = tune(ctx, reps, mode, out, run);
+    if (rc == GC_OK) cache_store(key, *out);
+    return rc;
 }
 
 }  // extern "C"

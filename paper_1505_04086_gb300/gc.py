@@ -102,7 +102,8 @@ class gc_server_info(ctypes.Structure):
                 ("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64),
                 ("peak_bytes", ctypes.c_int64), ("queued", ctypes.c_int32),
                 ("resident", ctypes.c_int32), ("max_wave_graphs", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32), ("cancelled", ctypes.c_uint64),
+                ("overlapped_waves", ctypes.c_uint64), ("overlap_us", ctypes.c_int64)]
 
 
 # Every function the header declares, with its ctypes signature.
@@ -138,6 +139,7 @@ _SIGS = {
     "gc_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(gc_stats)]),
     "gc_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.POINTER(gc_stats), ctypes.c_int32]),
     "gc_server_query": (ctypes.c_int, [_P, ctypes.POINTER(gc_server_info)]),
+    "gc_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "gc_server_destroy": (None, [_P]),
     "gc_color_noalloc": (ctypes.c_int, [ctypes.POINTER(gc_csr), ctypes.c_int32, ctypes.c_int64,
                                         ctypes.c_uint32, ctypes.POINTER(gc_opts), _P,
@@ -560,7 +562,11 @@ class Server:
         rc = load().gc_server_query(ctypes.c_void_p(self.handle), ctypes.byref(i))
         if rc != GC_OK:
             raise GCError(rc, "gc_server_query")
-        return {k: getattr(i, k) for k, _ in gc_server_info._fields_ if k != "pad"}
+        return {k: getattr(i, k) for k, _ in gc_server_info._fields_}
+
+    def cancel(self, ticket: int) -> int:
+        """Drop a request (gc_server_cancel); returns the status."""
+        return int(load().gc_server_cancel(ctypes.c_void_p(self.handle), ctypes.c_uint64(ticket)))
 
     def close(self):
         if self.handle:

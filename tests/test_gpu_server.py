@@ -138,3 +138,79 @@ def test_async_modes_valid_per_request(mode):
             assert O.check(g, col)[0] == 0
     finally:
         srv.close()
+
+
+def test_waves_run_side_by_side():
+    # A long request, then short ones behind it: with two compute lanes the
+    # short ones are coloured in a second wave while the first still runs.
+    # The overlap is measured on the GPU (event timestamps around each wave's
+    # colouring), and every result stays what the graph gives alone.
+    big = I.rmat(20, 16)
+    small = graphs(24, seed=9)
+    srv = gc.Server(0, budget_bytes=1 << 30, max_slots=256, mode=gc.GC_ALG_RSOC)
+    try:
+        assert srv.info()["lanes"] == 2
+        t_big = srv.submit(big.row_ptr, big.col_idx)
+        time.sleep(0.002)  # let the first wave start
+        ts = [srv.submit(g.row_ptr, g.col_idx) for g in small]
+        for g, t in zip(small, ts):
+            rc, col, _ = srv.wait(t, g.n, timeout_ms=60000)
+            assert rc == gc.GC_OK
+            assert np.array_equal(col, O.rsoc_det(g).colors)
+        rc, col, st = srv.wait(t_big, big.n, timeout_ms=60000)
+        assert rc == gc.GC_OK
+        ref = O.rsoc_det(big)
+        assert np.array_equal(col, ref.colors) and st["rounds"] == ref.iterations
+        info = srv.info()
+        assert info["waves"] >= 2
+        assert info["overlapped_waves"] >= 1 and info["overlap_us"] > 0, info
+    finally:
+        srv.close()
+
+
+def test_cancel():
+    gs = graphs(30, seed=11)
+    # one slot: everything but the first request stays queued for a while
+    srv = gc.Server(0, budget_bytes=64 << 20, max_slots=1, mode=gc.GC_ALG_RSOC)
+    try:
+        ts = [srv.submit(g.row_ptr, g.col_idx) for g in gs]
+        gone = ts[5::3]
+        for t in gone:
+            assert srv.cancel(t) == gc.GC_OK
+            assert srv.cancel(t) == gc.GC_ERR_NOT_FOUND
+            assert srv.poll(t, 1)[0] == gc.GC_ERR_NOT_FOUND
+        for g, t in zip(gs, ts):
+            if t in gone:
+                continue
+            rc, col, _ = srv.wait(t, g.n, timeout_ms=20000)
+            assert rc == gc.GC_OK
+            assert np.array_equal(col, O.rsoc_det(g).colors)
+        # a finished request can be dropped unpolled, and the server goes on
+        t = srv.submit(gs[0].row_ptr, gs[0].col_idx)
+        deadline = time.time() + 20
+        while time.time() < deadline:
+            i = srv.info()
+            if i["queued"] == 0 and i["resident"] == 0:
+                break
+            time.sleep(0.001)
+        assert srv.cancel(t) == gc.GC_OK
+        info = srv.info()
+        assert info["cancelled"] == len(gone) + 1
+        assert info["resident"] == 0 and info["in_use_bytes"] == 0
+        t = srv.submit(gs[1].row_ptr, gs[1].col_idx)
+        rc, col, _ = srv.wait(t, gs[1].n, timeout_ms=20000)
+        assert rc == gc.GC_OK and np.array_equal(col, O.rsoc_det(gs[1]).colors)
+        assert srv.cancel(12345678) == gc.GC_ERR_NOT_FOUND
+    finally:
+        srv.close()
+
+
+def test_cancel_in_flight_then_destroy():
+    # requests cancelled while on the GPU are released when their work ends,
+    # or by destroy
+    gs = graphs(20, seed=13)
+    srv = gc.Server(0, budget_bytes=256 << 20, max_slots=64, mode=gc.GC_ALG_RSOC | gc.GC_SCHED_ASYNC)
+    ts = [srv.submit(g.row_ptr, g.col_idx) for g in gs]
+    for t in ts:
+        assert srv.cancel(t) == gc.GC_OK
+    srv.close()
