@@ -1059,9 +1059,10 @@ __device__ __forceinline__ void stage_chunk(const KParams &p, Shared &sh, long l
 // staged copy): gives up after timeout_ns, setting GC_EW_TIMEOUT, and then
 // waits once more, as long again, so that a copy still in flight does not
 // land after the caller has moved on.  False on timeout.
-__device__ __noinline__ bool wait_mbar(const KParams &p, unsigned long long *bar, uint32_t par,
-                                       unsigned long long timeout_ns)
+__device__ __forceinline__ bool wait_mbar(const KParams &p, unsigned long long *bar, uint32_t par,
+                                          unsigned long long timeout_ns)
 {
+    if (mbar_try_wait(bar, par)) return true;
     const unsigned long long t0 = global_timer();
     while (!mbar_try_wait(bar, par)) {
         if (global_timer() - t0 > timeout_ns) {
@@ -1080,8 +1081,6 @@ __device__ __forceinline__ bool wait_stage(const KParams &p, Shared &sh, int slo
 {
     const uint32_t par = (phase >> slot) & 1u;
     phase ^= 1u << slot;
-    for (int k = 0; k < 1024; ++k)  // each try suspends the thread a while in hardware
-        if (mbar_try_wait(&sh.mbar[wid][slot], par)) return true;
     return wait_mbar(p, &sh.mbar[wid][slot], par, kStageTimeoutNs);
 }
 
@@ -2074,6 +2073,51 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
 }
 
 
+// The core phase of the asynchronous mode of one graph (all blocks; block 0
+// has just run plan_ordering): if the prologue found 1..kCoreMax core candidates and their
+// bit matrix fits, block 0 sorts them while the other blocks clear the
+// matrix, then all build it, then block 0 colours the core; else the
+// candidates join the hub list.  Ends with a grid barrier either way.
+// Returns the core's size (0: none).
+__device__ __noinline__ int core_stage(const KParams &p, Shared &sh, unsigned nbl, bool snap, long long &mb)
+{
+    DevState *st = p.st;
+    int core_n = 0;
+    {
+        const int H = ld_volatile(&st->core_count);
+        const int W = (H + 31) / 32;
+        if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
+            core_n = H;
+            if (blockIdx.x == 0) core_sort(p, sh, H);
+            if (nbl == 1 || blockIdx.x > 0) {
+                const long long words = (long long)32 * W * W;
+                const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
+                const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
+                for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
+            }
+        } else if (H > 0) {
+            // too many for a core: ordinary hubs, appended to the hub list
+            const int h0 = ld_volatile(&st->hub_all_count);
+            for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < H; i += (long long)nbl * kBlock)
+                if (h0 + i < p.hub_cap) __stcg(p.hub_all + h0 + i, __ldcg(p.mid_all + i));
+        }
+    }
+    grid_sync(st, nbl, kBarrierTimeoutNs, core_n > 0 ? 512 : 64);
+    if (core_n > 0 && ld_volatile(&st->error) == 0) {
+        core_build(p, core_n, mb);
+        grid_sync(st, nbl);
+        if (blockIdx.x == 0) {
+            const int M = core_colour(p, sh, core_n, snap ? p.cB : nullptr);
+            if (threadIdx.x == 0) {
+                st->core_n = core_n;
+                st->core_colors = M;
+            }
+        }
+        grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for block 0's serial work
+    }
+    return core_n;
+}
+
 template <bool ASYNC, bool BATCH>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
 {
@@ -2318,46 +2362,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
         const int window = p.window > 1 ? p.window : -1;
         int core_n = 0;
         if (ASYNC && alive && !recolor) {
-            // The core (see core_sort): sorted and marked by block 0 while the
-            // other blocks clear its bit matrix.
-            if (!BATCH && p.core_deg > 0) {
-                const int H = ld_volatile(&st->core_count);
-                const int W = (H + 31) / 32;
-                if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
-                    core_n = H;
-                    if (blockIdx.x == 0) core_sort(p, sh, H);
-                    if (nbl == 1 || blockIdx.x > 0) {
-                        const long long words = (long long)32 * W * W;
-                        const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
-                        const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
-                        for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
-                    }
-                } else if (H > 0) {
-                    // too many for a core: ordinary hubs, appended to the hub list
-                    const int h0 = ld_volatile(&st->hub_all_count);
-                    for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < H; i += (long long)nbl * kBlock)
-                        if (h0 + i < p.hub_cap) __stcg(p.hub_all + h0 + i, __ldcg(p.mid_all + i));
-                }
-            }
             // Ids of a naturally numbered mesh are local: neighbours would be
             // coloured concurrently unless the graph goes strictly in id order.
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
-            grid_sync(st, nbl, kBarrierTimeoutNs, core_n > 0 ? 512 : 64);
+            // The core of one graph (see core_sort); its first barrier also
+            // ends plan_ordering.
+            if (!BATCH && p.core_deg > 0) core_n = core_stage(p, sh, nbl, snap, mb);
+            else grid_sync(st, nbl);
             alive = ld_volatile(&st->error) == 0;
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
-            if (core_n > 0 && alive) {
-                core_build(p, core_n, mb);
-                grid_sync(st, nbl);
-                if (blockIdx.x == 0) {
-                    const int M = core_colour(p, sh, core_n, snap ? p.cB : nullptr);
-                    if (threadIdx.x == 0) {
-                        st->core_n = core_n;
-                        st->core_colors = M;
-                    }
-                }
-                grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for block 0's serial work
-                alive = ld_volatile(&st->error) == 0;
-            }
         }
 
         // Stages: one (all of V), or, with tiers, hubs -> mid degree -> low
