@@ -415,6 +415,7 @@ __device__ void push_clashes_warp(const KParams &p, int32_t v, int64_t beg, int6
 
 constexpr int kWarpUnroll = 4;   // entries per lane in flight (warp path)
 constexpr int kBlockUnroll = 4;  // entries per thread in flight (block path)
+constexpr int kSusBuf = 64;      // round 0: suspects a warp collects before one append
 
 template <bool ASYNC>
 __device__ bool detect_warp(const KParams &p, int32_t v, int64_t beg, int64_t end, int32_t nbase,
@@ -506,6 +507,7 @@ struct Shared {
     } slot[kWarps][2];
     uint32_t warp_bm[kWarps][kWarpBmWords];
     uint32_t hub_bm[kHubBmWords];
+    int32_t sus[kWarps][kSusBuf];            // round 0: suspects of the warp not yet appended
     int found;                               // detect_block: a conflict was seen
     int first;
     int tcount;
@@ -960,6 +962,48 @@ __device__ __forceinline__ void push_lanes(const KParams &p, bool d, int32_t v, 
         else atomicOr(&st->error, GC_EW_OVERFLOW);
         if (stats) note_push_graph<BATCH>(p, g, it);
     }
+}
+
+// Round 0's suspects of one warp, collected in shared memory and appended to
+// the worklist of iteration `it` kSusBuf at a time: one atomic per flush
+// instead of one per chunk, off the chunk's critical path.
+struct SusBuf {
+    int n = 0;                       // entries held (warp-uniform)
+    unsigned long long work = 0;     // their degree sum (warp-uniform)
+};
+
+__device__ __forceinline__ void sus_flush(const KParams &p, Shared &sh, SusBuf &b, int it, int lane, int wid)
+{
+    if (b.n == 0) return;
+    DevState *st = p.st;
+    int ob = 0;
+    if (lane == 0)
+        ob = (int)(atomicAdd(&st->wl_packed[it & (kRing - 1)], ((unsigned long long)b.n << kWorkBits) + b.work) >>
+                   kWorkBits);
+    ob = __shfl_sync(FULL_MASK, ob, 0);
+    for (int i = lane; i < b.n; i += 32) {
+        const int o = ob + i;
+        if (o < p.n) __stcg(p.wl[it & 1] + o, sh.sus[wid][i]);
+        else atomicOr(&st->error, GC_EW_OVERFLOW);
+    }
+    __syncwarp();
+    b.n = 0;
+    b.work = 0;
+}
+
+// Add the lanes with d set (keepers: those not queued yet) to the buffer.
+__device__ __forceinline__ void sus_push(const KParams &p, Shared &sh, SusBuf &b, bool d, int32_t v, int deg, int it,
+                                         int lane, int wid)
+{
+    if (d && (p.mode & GC_FF_KEEPERS)) d = claim_push(p, v, it);
+    const unsigned m = __ballot_sync(FULL_MASK, d);
+    if (!m) return;
+    const int k = __popc(m);
+    if (b.n + k > kSusBuf) sus_flush(p, sh, b, it, lane, wid);
+    if (d) sh.sus[wid][b.n + __popc(m & ((1u << lane) - 1u))] = v;
+    b.work += (unsigned long long)__reduce_add_sync(FULL_MASK, d ? (unsigned)deg : 0u);
+    b.n += k;
+    __syncwarp();
 }
 
 // One chunk of up to 32 worklist entries, one per lane (v = -1: none):
@@ -1431,6 +1475,7 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
     if (lane == 0) t = atomicAdd(claim, 1);
     t = __shfl_sync(FULL_MASK, t, 0);
     LaneRow cur, nxt;
+    SusBuf sbuf;
     int slot = 0;
     {
         long long cb = -1, cend = 0;
@@ -1439,7 +1484,10 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
     }
     for (;;) {
         const long long cb = sh.slot[wid][slot].cb;
-        if (cb < 0) break;
+        if (cb < 0) {
+            if (ordered && push) sus_flush(p, sh, sbuf, it, lane, wid);
+            break;
+        }
         const long long soff = sh.slot[wid][slot].soff;
         const int tile = sh.slot[wid][slot].tile;
         const int kin = sh.slot[wid][slot].kin;
@@ -1492,7 +1540,7 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
                                         push, mb, lane, wid);
         }
         // Round 0 with push: the suspects form the first repair worklist.
-        if (ordered && push) push_lanes<BATCH>(p, sus, v, cur.deg, cur.g, it, lane, false);
+        if (ordered && push) sus_push(p, sh, sbuf, sus, v, cur.deg, it, lane, wid);
         if (ordered && window > 0 && last_of_tile) publish_tile_done(p, tile, lane);
         __syncwarp();  // every lane is done with seg[slot] before it is refilled
         cur = nxt;
@@ -1530,6 +1578,8 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
+            // the core was coloured before round 0 and never changes
+            if (!BATCH && p.core_deg > 0 && end - beg > p.core_deg && ld_volatile(&st->core_n) > 0) continue;
             bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
                      op == OP_TENT;  // round 0: hubs are kept for the first repair pass
             if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
@@ -2074,32 +2124,51 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
 
 
 // The core phase of the asynchronous mode of one graph (all blocks; block 0
-// has just run plan_ordering): if the prologue found 1..kCoreMax core candidates and their
-// bit matrix fits, block 0 sorts them while the other blocks clear the
-// matrix, then all build it, then block 0 colours the core; else the
-// candidates join the hub list.  Ends with a grid barrier either way.
-// Returns the core's size (0: none).
-__device__ __noinline__ int core_stage(const KParams &p, Shared &sh, unsigned nbl, bool snap, long long &mb)
+// has just run plan_ordering): the hubs of degree > core_deg are listed; if
+// there are 1..kCoreMax of them and their bit matrix fits, block 0 sorts them
+// while the other blocks clear the matrix, then all build it, then block 0
+// colours the core (the hub pass then skips them); else they stay ordinary
+// hubs.  Ends with a grid barrier either way; st->core_n is the core's size
+// (0: none).
+__device__ __noinline__ void core_stage(const KParams &p, Shared &sh)
 {
     DevState *st = p.st;
+    const unsigned nbl = gridDim.x;
+    const bool snap = (p.mode & GC_REPAIR_SNAPSHOT) && !(p.mode & GC_ALG_TWO_PHASE);
+    long long mb = 0;
     int core_n = 0;
-    {
-        const int H = ld_volatile(&st->core_count);
-        const int W = (H + 31) / 32;
-        if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
-            core_n = H;
-            if (blockIdx.x == 0) core_sort(p, sh, H);
-            if (nbl == 1 || blockIdx.x > 0) {
-                const long long words = (long long)32 * W * W;
-                const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
-                const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
-                for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
-            }
-        } else if (H > 0) {
-            // too many for a core: ordinary hubs, appended to the hub list
-            const int h0 = ld_volatile(&st->hub_all_count);
-            for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < H; i += (long long)nbl * kBlock)
-                if (h0 + i < p.hub_cap) __stcg(p.hub_all + h0 + i, __ldcg(p.mid_all + i));
+    // the candidates: hubs of degree > core_deg, listed in p.mid_all
+    const int nh = ld_volatile(&st->hub_all_count);
+    for (int i0 = blockIdx.x * kBlock; i0 < nh; i0 += nbl * kBlock) {
+        const int i = i0 + threadIdx.x;
+        bool cand = false;
+        int32_t v = 0;
+        if (i < nh) {
+            v = __ldcg(p.hub_all + i);
+            cand = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v) > p.core_deg;
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, cand);
+        if (m) {
+            const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+            int ob = 0;
+            if (lane == leader) ob = atomicAdd(&st->core_count, __popc(m));
+            ob = __shfl_sync(FULL_MASK, ob, leader);
+            if (cand) __stcg(p.mid_all + ob + __popc(m & ((1u << lane) - 1u)), v);
+        }
+    }
+    grid_sync(st, nbl);
+    const int H = ld_volatile(&st->core_count);
+    const int W = (H + 31) / 32;
+    // more than kCoreMax, or a bit matrix larger than a worklist buffer: no
+    // core (the candidates stay ordinary hubs)
+    if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
+        core_n = H;
+        if (blockIdx.x == 0) core_sort(p, sh, H);
+        if (nbl == 1 || blockIdx.x > 0) {
+            const long long words = (long long)32 * W * W;
+            const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
+            const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
+            for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
         }
     }
     grid_sync(st, nbl, kBarrierTimeoutNs, core_n > 0 ? 512 : 64);
@@ -2115,36 +2184,27 @@ __device__ __noinline__ int core_stage(const KParams &p, Shared &sh, unsigned nb
         }
         grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for block 0's serial work
     }
-    return core_n;
+    for (int o = 16; o > 0; o >>= 1) mb += __shfl_down_sync(FULL_MASK, mb, o);
+    if ((threadIdx.x & 31) == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
 }
 
+// The prologue of a colouring launch (all blocks): degree binning of V (hub lists),
+// colour initialisation, per-graph statistics, the ordered round-0 plan
+// and the core (asynchronous), or the first worklist of an incremental
+// recolouring.  Ends with a grid barrier; its byte-model count goes to the
+// launch state directly.
 template <bool ASYNC, bool BATCH>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
+__device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
 {
-    extern __shared__ __align__(128) unsigned char gc_smem[];
-    Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
     DevState *st = p.st;
     const int lane = threadIdx.x & 31;
     const bool twop = (p.mode & GC_ALG_TWO_PHASE) != 0;
-    // Snapshot rounds: deterministic mode, or asynchronous round 0 followed
-    // by round-synchronous repair rounds (GC_REPAIR_SNAPSHOT, RSOC only).
-    const bool snap = !twop && (!ASYNC || (p.mode & GC_REPAIR_SNAPSHOT) != 0);
-    // Degree tiers (asynchronous RSOC): hubs, then mid-degree, then the rest.
     const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
     const bool keep = ASYNC && (p.mode & GC_FF_KEEPERS) != 0;
-    const bool recolor = p.touched != nullptr;  // incremental: start from the given colours
-    unsigned nbl = gridDim.x;
+    const bool recolor = p.touched != nullptr;
+    const unsigned nbl = gridDim.x;
     long long mb = 0;
-    uint32_t phase = 0;  // parity bits of this warp's two staging barriers
-    if (lane == 0) {
-        mbar_init(&sh.mbar[threadIdx.x >> 5][0], 1);
-        mbar_init(&sh.mbar[threadIdx.x >> 5][1], 1);
-        fence_mbarrier_init();
-    }
-    __syncwarp();
-
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start = global_timer();
-    if (ld_volatile(&st->error) == 0) {
+    {
         // Prologue: degree binning of V (hub list) and colour initialisation.
         // Deterministic round 0 colours every vertex from a snapshot in which
         // nothing is coloured yet, so every vertex gets colour 1.
@@ -2212,14 +2272,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
 #pragma unroll
             for (int u = 0; u < kProU; ++u) {
                 const long long vi = b0 + u * stride + threadIdx.x;
-                bool hub = false, midv = false, corev = false;
+                bool hub = false, midv = false;
                 const int32_t v = (int32_t)vi;
                 if (vi < p.n) {
                     const int64_t deg = degs[u];
                     const int32_t g = gs[u];
                     hub = deg > p.t2;
                     midv = tiers && !hub && deg > p.t1;
-                    corev = hub && p.core_deg > 0 && deg > p.core_deg;
                     if (hub && ASYNC) atomicAdd(&p.gstat[g].hubs, 1u);
                     if (ASYNC && !hub && deg > kT1Max && __ldcg(&p.gstat[g].wide) == 0u)
                         atomicOr(&p.gstat[g].wide, 1u);
@@ -2228,29 +2287,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
                     if (!ASYNC) mb += 4;
                     if (keep) p.mark[v] = 0;
                 }
-                const unsigned m = __ballot_sync(FULL_MASK, hub && !corev);
+                const unsigned m = __ballot_sync(FULL_MASK, hub);
                 if (m) {
                     const int leader = __ffs(m) - 1;
                     int ob = 0;
                     if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
                     ob = __shfl_sync(FULL_MASK, ob, leader);
-                    if (hub && !corev) {
+                    if (hub) {
                         const int o = ob + __popc(m & ((1u << lane) - 1u));
                         if (o < p.hub_cap) __stcg(p.hub_all + o, v);
-                        else atomicOr(&st->error, GC_EW_OVERFLOW);
-                    }
-                }
-                // core candidates: listed apart (coloured first if they fit,
-                // else taken by the hub pass after hub_all)
-                const unsigned mc = __ballot_sync(FULL_MASK, corev);
-                if (mc) {
-                    const int leader = __ffs(mc) - 1;
-                    int ob = 0;
-                    if (lane == leader) ob = atomicAdd(&st->core_count, __popc(mc));
-                    ob = __shfl_sync(FULL_MASK, ob, leader);
-                    if (corev) {
-                        const int o = ob + __popc(mc & ((1u << lane) - 1u));
-                        if (o < p.n) __stcg(p.mid_all + o, v);
                         else atomicOr(&st->error, GC_EW_OVERFLOW);
                     }
                 }
@@ -2353,6 +2398,52 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
             grid_sync(st, nbl);
         }
 
+        if (ASYNC && ld_volatile(&st->error) == 0 && !recolor) {
+            // Ids of a naturally numbered mesh are local: neighbours would be
+            // coloured concurrently unless the graph goes strictly in id order.
+            if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
+            // The core of one graph (see core_sort); its first barrier also
+            // ends plan_ordering.
+            if (!BATCH && p.core_deg > 0 && ld_volatile(&st->hub_all_count) > 0)
+                core_stage(p, sh);
+            else
+                grid_sync(st, nbl);
+            if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
+        }
+
+    }
+    for (int o = 16; o > 0; o >>= 1) mb += __shfl_down_sync(FULL_MASK, mb, o);
+    if (lane == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
+}
+
+
+template <bool ASYNC, bool BATCH>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
+{
+    extern __shared__ __align__(128) unsigned char gc_smem[];
+    Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
+    DevState *st = p.st;
+    const int lane = threadIdx.x & 31;
+    const bool twop = (p.mode & GC_ALG_TWO_PHASE) != 0;
+    // Snapshot rounds: deterministic mode, or asynchronous round 0 followed
+    // by round-synchronous repair rounds (GC_REPAIR_SNAPSHOT, RSOC only).
+    const bool snap = !twop && (!ASYNC || (p.mode & GC_REPAIR_SNAPSHOT) != 0);
+    // Degree tiers (asynchronous RSOC): hubs, then mid-degree, then the rest.
+    const bool tiers = ASYNC && !twop && (p.mode & GC_TIERS) != 0;
+    const bool recolor = p.touched != nullptr;  // incremental: start from the given colours
+    unsigned nbl = gridDim.x;
+    long long mb = 0;
+    uint32_t phase = 0;  // parity bits of this warp's two staging barriers
+    if (lane == 0) {
+        mbar_init(&sh.mbar[threadIdx.x >> 5][0], 1);
+        mbar_init(&sh.mbar[threadIdx.x >> 5][1], 1);
+        fence_mbarrier_init();
+    }
+    __syncwarp();
+
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start = global_timer();
+    if (ld_volatile(&st->error) == 0) {
+        prologue<ASYNC, BATCH>(p, sh);
         bool alive = ld_volatile(&st->error) == 0;
         const int hub_all_n = ld_volatile(&st->hub_all_count);
         const int mid_all_n = ld_volatile(&st->mid_all_count);
@@ -2360,18 +2451,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
         // Tile window for the round-0 pass over the graphs that are not
         // coloured in id order by one warp (window > 1 only).
         const int window = p.window > 1 ? p.window : -1;
-        int core_n = 0;
-        if (ASYNC && alive && !recolor) {
-            // Ids of a naturally numbered mesh are local: neighbours would be
-            // coloured concurrently unless the graph goes strictly in id order.
-            if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
-            // The core of one graph (see core_sort); its first barrier also
-            // ends plan_ordering.
-            if (!BATCH && p.core_deg > 0) core_n = core_stage(p, sh, nbl, snap, mb);
-            else grid_sync(st, nbl);
-            alive = ld_volatile(&st->error) == 0;
-            if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
-        }
 
         // Stages: one (all of V), or, with tiers, hubs -> mid degree -> low
         // degree, each taken through round 0 and its repair rounds before the
@@ -2386,9 +2465,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
             stages[2] = PassIn{true, nullptr, p.n, nullptr, 0, p.t1};
             nstages = 3;
         } else {
-            // core candidates that were not coloured as a core joined the hub list
-            const int extra = (!BATCH && p.core_deg > 0 && core_n == 0) ? ld_volatile(&st->core_count) : 0;
-            stages[0] = PassIn{true, nullptr, p.n, p.hub_all, hub_all_n + extra, p.t2};
+            stages[0] = PassIn{true, nullptr, p.n, p.hub_all, hub_all_n, p.t2};
         }
 
         int32_t *R = p.cA;
