@@ -2417,6 +2417,20 @@ __device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
 }
 
 
+// The prologue of a colouring as a launch of its own (degree binning,
+// colour initialisation, the round-0 plan and the core), so that the
+// rounds' kernel below is compiled without the core's code and calls.
+template <bool ASYNC, bool BATCH>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) prologue_kernel(KParams p)
+{
+    extern __shared__ __align__(128) unsigned char gc_smem[];
+    Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
+    DevState *st = p.st;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start = global_timer();
+    if (ld_volatile(&st->error) == 0) prologue<ASYNC, BATCH>(p, sh);
+}
+
+// All rounds of a colouring (after prologue_kernel on the same stream).
 template <bool ASYNC, bool BATCH>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
 {
@@ -2441,10 +2455,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
     }
     __syncwarp();
 
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_start = global_timer();
     if (ld_volatile(&st->error) == 0) {
-        prologue<ASYNC, BATCH>(p, sh);
-        bool alive = ld_volatile(&st->error) == 0;
+        bool alive = true;
         const int hub_all_n = ld_volatile(&st->hub_all_count);
         const int mid_all_n = ld_volatile(&st->mid_all_count);
         int q = 0;
@@ -2733,7 +2745,9 @@ static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, color_kernel<A, B>, p);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, prologue_kernel<A, B>, p);
+    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, color_kernel<A, B>, p);
+    return e;
 }
 
 cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s)
@@ -2748,24 +2762,37 @@ static const void *color_kernel_ptr(bool async, bool batch)
                  : (batch ? (const void *)color_kernel<false, true> : (const void *)color_kernel<false, false>);
 }
 
+static const void *prologue_kernel_ptr(bool async, bool batch)
+{
+    return async ? (batch ? (const void *)prologue_kernel<true, true> : (const void *)prologue_kernel<true, false>)
+                 : (batch ? (const void *)prologue_kernel<false, true> : (const void *)prologue_kernel<false, false>);
+}
+
 cudaError_t prepare_color_kernels()
 {
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            const cudaError_t e = cudaFuncSetAttribute(color_kernel_ptr(a, b),
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)sizeof(Shared));
-            if (e != cudaSuccess) return e;
-        }
+        for (int b = 0; b < 2; ++b)
+            for (const void *f : {color_kernel_ptr(a, b), prologue_kernel_ptr(a, b)}) {
+                const cudaError_t e =
+                    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
+// Blocks per SM both launches of a colouring can hold (the grid of each is
+// cooperative: all its blocks resident at once).
 cudaError_t query_occupancy(bool async, bool batch, int *blocks_per_sm)
 {
-    const cudaError_t e = prepare_color_kernels();
+    cudaError_t e = prepare_color_kernels();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, color_kernel_ptr(async, batch), kBlock,
-                                                         sizeof(Shared));
+    int a = 0, b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, color_kernel_ptr(async, batch), kBlock, sizeof(Shared));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, prologue_kernel_ptr(async, batch), kBlock,
+                                                          sizeof(Shared));
+    *blocks_per_sm = a < b ? a : b;
+    return e;
 }
 
 size_t color_smem_bytes() { return sizeof(Shared); }
