@@ -226,19 +226,20 @@ typedef struct {
                                     neighbours' degrees) than this is inspected
                                     by a whole block, the others by one warp;
                                     0 = 4096 */
-    int32_t core_deg;            /* GC_SCHED_ASYNC on one graph (gc_color,
-                                    gc_color_async, gc_color_noalloc; not
-                                    with GC_TIERS, GC_FF_KEEPERS or GC_DIST2):
+    int32_t core_deg;            /* GC_SCHED_ASYNC (every colouring call
+                                    except recolouring; not with GC_TIERS,
+                                    GC_FF_KEEPERS or GC_DIST2): in each graph
                                     the vertices of degree above max(core_deg,
                                     t2) -- if there are at most 4096 of them --
-                                    form the core, coloured before round 0 one
+                                    form its core, coloured before round 0 one
                                     at a time in decreasing degree (ties:
                                     increasing id) by First-Fit among
                                     themselves; they keep those colours, so
                                     the repair rounds never rescan their rows
                                     and a dense core of hubs (R-MAT) does not
-                                    drive the colour count up.  0 = 4096,
-                                    -1 = no core */
+                                    drive the colour count up.  The cores of a
+                                    batch are coloured side by side, one block
+                                    each.  0 = 4096, -1 = no core */
 } gc_opts;
 
 typedef struct gc_ctx gc_ctx;

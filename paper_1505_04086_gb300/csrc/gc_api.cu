@@ -134,7 +134,7 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     const bool masks = async && !batch && !(mode & (GC_ALG_TWO_PHASE | GC_TIERS | GC_FF_KEEPERS | GC_REPAIR_SNAPSHOT |
                                                      GC_DIST2)) && p.touched == nullptr;
     p.r0mask = masks ? c->r0mask.as<uint64_t>() : nullptr;
-    p.core_deg = gc::core_applies(mode, batch, p.touched != nullptr) ? r.core_deg : 0;
+    p.core_deg = gc::core_applies(mode, p.touched != nullptr) ? r.core_deg : 0;
     p.done = c->done.as<int32_t>();
     p.gstat = c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();

@@ -57,12 +57,12 @@ inline bool mode_ok(uint32_t mode)
 // (batches, plans, the server, the no-alloc and recolour calls, autotuning).
 inline bool dist1_mode_ok(uint32_t mode) { return mode_ok(mode) && !(mode & GC_DIST2); }
 
-// Whether a colouring in this mode colours the core of high-degree vertices
-// first (asynchronous, one graph, a full colouring, the plain First-Fit
+// Whether a colouring in this mode colours each graph's core of high-degree
+// vertices first (asynchronous, a full colouring, the plain First-Fit
 // choices of Algorithm 2 or 3 and one stage for all degrees).
-inline bool core_applies(uint32_t mode, bool batch, bool recolor)
+inline bool core_applies(uint32_t mode, bool recolor)
 {
-    return (mode & GC_SCHED_ASYNC) && !batch && !recolor && !(mode & (GC_TIERS | GC_FF_KEEPERS | GC_DIST2));
+    return (mode & GC_SCHED_ASYNC) && !recolor && !(mode & (GC_TIERS | GC_FF_KEEPERS | GC_DIST2));
 }
 
 // The second n-entry buffer holds colours (deterministic mode, snapshot
@@ -83,6 +83,11 @@ struct GraphStat {
     unsigned int ordered;           // coloured in id order in round 0
     unsigned int wide;              // nonzero: some vertex has kT1Max < degree <= t2
     unsigned int group;             // warps colouring it in id order together (0: one)
+    int core_cnt;                   // its hubs of degree > core_deg (core candidates)
+    int core_fill;                  // candidates listed so far
+    int core_on;                    // nonzero: its core is coloured before round 0
+    int core_off;                   // first entry of its core in the core list
+    int core_bofs;                  // first word of its core's bit matrix
 };
 
 // Device-resident state of one colouring launch.  Zeroed before each launch.
@@ -115,10 +120,11 @@ struct DevState {
     int d2_hcount[kRing];            // distance-2: heavy vertices pushed per iteration
     int d2_hclaim[kRing];            // distance-2: heavy vertices claimed per iteration
     int d2_hclaim0;                  // distance-2: heavy vertices claimed in round 0
-    int core_count;                  // vertices of degree > core_deg found by the prologue
-    int core_n;                      // of which coloured as the core before round 0 (0: no core)
+    int core_count;                  // entries of the core list (all graphs' cores)
+    int core_n;                      // core sorting: next graph to claim
     int core_task;                   // core adjacency build: next task
-    int core_colors;                 // largest colour of the core
+    int core_colors;                 // core colouring: next graph to claim
+    long long core_words;            // words of the cores' bit matrices
 };
 
 struct KParams {
@@ -167,7 +173,7 @@ struct KParams {
     int32_t d2_heavy;          // distance 2: two-hop entries above which a block inspects a vertex
     uint64_t *r0mask;          // asynchronous round 0 of one graph: per suspect, the row positions of the
                                // tie-side neighbours read as uncoloured (null: not kept)
-    int32_t core_deg;          // asynchronous single graph: vertices of degree > core_deg (and > t2) are
+    int32_t core_deg;          // asynchronous: each graph's vertices of degree > core_deg (and > t2) are
                                // coloured first, one at a time in decreasing degree (0: no core)
 };
 

@@ -1578,8 +1578,8 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
-            // the core was coloured before round 0 and never changes
-            if (!BATCH && p.core_deg > 0 && end - beg > p.core_deg && ld_volatile(&st->core_n) > 0) continue;
+            // a core was coloured before round 0 and never changes
+            if (p.core_deg > 0 && end - beg > p.core_deg && __ldcg(&p.gstat[g].core_on)) continue;
             bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
                      op == OP_TENT;  // round 0: hubs are kept for the first repair pass
             if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
@@ -1802,12 +1802,15 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
 // vertex avoids them), so the repair rounds never rescan a hub row, and the
 // colour count stays close to sequential First-Fit (the core decides it).
 //
-// Data: p.mid_all lists the core (rank order after core_sort); while the
-// core is built, a core vertex's colour slot holds -(rank + 1); p.wl[1]
-// holds the core's adjacency as a bit matrix, word w of rank r at
+// Every graph of a launch has its own core (a batch's R-MAT requests as
+// much as a single R-MAT graph).  Data: p.mid_all lists the cores, graph
+// after graph (GraphStat::core_off), each in rank order after core_sort, and
+// p.hub[0] the graph of each entry; while the cores are built, a core
+// vertex's colour slot holds -(rank + 1); p.wl[1] holds each core's adjacency
+// as a bit matrix from word GraphStat::core_bofs on, word w of rank r at
 // w * Hp + r, Hp = H rounded up to a multiple of 32 (column-major: the 32
-// ranks of a batch are one coalesced read);
-// p.hub[1][r] is the first adjacency-build task of rank r (H + 1 entries).
+// ranks of a colouring batch are one coalesced read); p.hub[1][i] is the
+// first adjacency-build task of entry i (one entry more at the end).
 
 // Exclusive prefix sum over the block of one value per thread (all threads
 // call it); `scratch` holds kWarps ints of shared memory.
@@ -1833,9 +1836,11 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int *scratch, int &to
     return before + incl - x;
 }
 
-// Block 0: sort the core by (degree descending, id ascending), write it back
-// in rank order, mark the colour slots and list the build tasks.
-__device__ __noinline__ void core_sort(const KParams &p, Shared &sh, int H)
+// One block: sort a core (list, H entries) by (degree descending, id
+// ascending), write it back in rank order, mark the colour slots with the
+// ranks and store each entry's number of build tasks in tasks[].
+template <bool BATCH>
+__device__ __noinline__ void core_sort(const KParams &p, Shared &sh, int32_t *list, int H, int32_t *tasks)
 {
     unsigned long long *key = reinterpret_cast<unsigned long long *>(&sh.seg[0][0][0]);  // kCoreMax keys
     static_assert(sizeof(sh.seg) >= kCoreMax * sizeof(unsigned long long), "core keys fit the staging area");
@@ -1844,9 +1849,11 @@ __device__ __noinline__ void core_sort(const KParams &p, Shared &sh, int H)
     for (int i = threadIdx.x; i < P; i += kBlock) {
         unsigned long long k = ~0ull;
         if (i < H) {
-            const int32_t v = __ldcg(p.mid_all + i);
-            const int32_t d = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
-            k = ((unsigned long long)(~(uint32_t)d) << 32) | (uint32_t)v;
+            const int32_t v = __ldcg(list + i);
+            int64_t beg, end;
+            int32_t nbase, g;
+            row_of<BATCH>(p, v, beg, end, nbase, g);
+            k = ((unsigned long long)(~(uint32_t)(end - beg)) << 32) | (uint32_t)v;
         }
         key[i] = k;
     }
@@ -1867,68 +1874,69 @@ __device__ __noinline__ void core_sort(const KParams &p, Shared &sh, int H)
         }
     for (int r = threadIdx.x; r < H; r += kBlock) {
         const int32_t v = (int32_t)(uint32_t)key[r];
-        __stcg(p.mid_all + r, v);
+        const int d = (int)~(uint32_t)(key[r] >> 32);
+        __stcg(list + r, v);
+        __stcg(tasks + r, (d + kCoreSeg - 1) / kCoreSeg);
         st_color<true>(p.cA + v, -(r + 1));
     }
-    // tasks of kCoreSeg adjacency entries per rank, prefix-summed into p.hub[1]
-    constexpr int kPer = kCoreMax / kBlock;
-    int tasks[kPer];
-    int sum = 0;
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const int r = threadIdx.x * kPer + q;
-        tasks[q] = 0;
-        if (r < H) {
-            const int d = (int)~(uint32_t)(key[r] >> 32);
-            tasks[q] = (d + kCoreSeg - 1) / kCoreSeg;
-        }
-        sum += tasks[q];
-    }
-    int total;
-    int before = block_exclusive_scan(sum, reinterpret_cast<int *>(sh.warp_bm), total);
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const int r = threadIdx.x * kPer + q;
-        if (r < H) __stcg(p.hub[1] + r, before);
-        before += tasks[q];
-    }
-    if (threadIdx.x == 0) __stcg(p.hub[1] + H, total);
     __syncthreads();
 }
 
-// All blocks: the core's adjacency bit matrix, from the core vertices' rows
-// (a neighbour is in the core when its colour slot holds a rank mark).
-// Tasks of kCoreSeg entries are claimed warp by warp.
-__device__ __noinline__ void core_build(const KParams &p, int H, long long &mb)
+// One block: exclusive prefix sum of x[0..T) in place, x[T] = the total.
+__device__ __noinline__ void block_scan_inplace(int32_t *x, int T, Shared &sh)
+{
+    int carry = 0;
+    for (int i0 = 0; i0 < T; i0 += kBlock) {
+        const int i = i0 + threadIdx.x;
+        const int v = i < T ? __ldcg(x + i) : 0;
+        int total;
+        const int before = block_exclusive_scan(v, reinterpret_cast<int *>(sh.warp_bm), total);
+        if (i < T) __stcg(x + i, carry + before);
+        carry += total;
+    }
+    if (threadIdx.x == 0) __stcg(x + T, carry);
+    __syncthreads();
+}
+
+// All blocks: the cores' adjacency bit matrices, from the core vertices'
+// rows (a neighbour is in its graph's core when its colour slot holds a rank
+// mark).  Tasks of kCoreSeg entries are claimed warp by warp.
+template <bool BATCH>
+__device__ __noinline__ void core_build(const KParams &p, int T, long long &mb)
 {
     const int lane = threadIdx.x & 31;
     const int32_t *tpfx = p.hub[1];
-    const int T = __ldcg(tpfx + H);
-    uint32_t *bits = reinterpret_cast<uint32_t *>(p.wl[1]);
-    const int Hp = (H + 31) & ~31;  // column stride: word w of rank r at w * Hp + r
+    const int ntask = __ldcg(tpfx + T);
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&p.st->core_task, 1);
         t = __shfl_sync(FULL_MASK, t, 0);
-        if (t >= T) break;
-        int lo = 0, hi = H - 1;  // the rank whose tasks hold t
+        if (t >= ntask) break;
+        int lo = 0, hi = T - 1;  // the entry whose tasks hold t
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (__ldcg(tpfx + mid) <= t) lo = mid;
             else hi = mid - 1;
         }
-        const int r = lo;
-        const int k = t - __ldcg(tpfx + r);
-        const int32_t v = __ldcg(p.mid_all + r);
-        const int32_t rb = __ldg(p.row_ptr + v), re = __ldg(p.row_ptr + v + 1);
-        const int32_t beg = rb + k * kCoreSeg;
-        const int32_t end = min(re, beg + kCoreSeg);
-        for (int32_t i0 = beg; i0 < end; i0 += 32 * kUnroll) {
+        const int i = lo;
+        const int k = t - __ldcg(tpfx + i);
+        const int32_t v = __ldcg(p.mid_all + i);
+        const int gg = BATCH ? __ldcg(p.hub[0] + i) : 0;
+        const GraphStat &gs = p.gstat[gg];
+        const int r = i - gs.core_off;
+        const int Hp = (gs.core_cnt + 31) & ~31;  // column stride: word w of rank r at w * Hp + r
+        uint32_t *bits = reinterpret_cast<uint32_t *>(p.wl[1]) + gs.core_bofs;
+        int64_t rb, re;
+        int32_t nbase, g;
+        row_of<BATCH>(p, v, rb, re, nbase, g);
+        const int64_t beg = rb + (int64_t)k * kCoreSeg;
+        const int64_t end = min(re, beg + kCoreSeg);
+        for (int64_t i0 = beg; i0 < end; i0 += 32 * kUnroll) {
             int32_t u[kUnroll];
 #pragma unroll
             for (int q = 0; q < kUnroll; ++q) {
-                const int32_t i = i0 + q * 32 + lane;
-                u[q] = i < end ? __ldg(p.col_idx + i) : -1;
+                const int64_t e = i0 + q * 32 + lane;
+                u[q] = e < end ? nbase + __ldg(p.col_idx + e) : -1;
             }
             int c[kUnroll];
 #pragma unroll
@@ -1964,18 +1972,6 @@ __device__ __forceinline__ int first_free_warp(const uint32_t *Fl, int Fw, int l
     return Fw * 32;  // not reached: Fw words cover colours up to H+1
 }
 
-// Block 0: sequential First-Fit over the core in rank order, 32 ranks at a
-// time.  First every vertex of the batch collects the colours of its core
-// neighbours in earlier batches (all warps; a thread's bit words are loaded
-// one batch ahead), then warp 0 resolves the batch in rank order: vertex k
-// adds the colours just given to its lower-ranked neighbours in the batch
-// and takes the first colour left.  While every colour stays below
-// kMarkColours the collected colours are byte tags in a row per vertex
-// (plain stores of the batch's tag: the warps that share a row all store the
-// same value; a warp finds the first untagged colour, 16 per lane at a
-// time), else bits in a bitset row (atomics).  The colours go to p.cA and, if not
-// null, to `also` (the second buffer of snapshot repairs, which only
-// inspected vertices are written to).  Returns the largest colour.
 // The bytes of w that differ from the tag byte (t4 = tag in all four), as
 // bits 0..3: the high bit of ((v & 0x7f..) + 0x7f..) | v is set exactly in the
 // non-zero bytes of v (no carry crosses a byte), and the multiply gathers
@@ -1990,7 +1986,8 @@ __device__ __forceinline__ uint32_t untagged4(uint32_t w, uint32_t t4)
 
 constexpr int kMarkColours = 1024;              // colours the byte rows cover
 constexpr int kMarkStride = kMarkColours + 16;  // bytes per row (16-byte aligned, rows on different banks)
-__device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int32_t *also)
+__device__ __noinline__ int core_colour(const KParams &p, Shared &sh, const int32_t *list, const uint32_t *bits, int H,
+                                       int32_t *also)
 {
     static_assert(offsetof(Shared, ring) == sizeof(sh.seg), "staging area and ring are contiguous");
     unsigned char *area = reinterpret_cast<unsigned char *>(&sh.seg[0][0][0]);
@@ -2003,7 +2000,6 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
     static_assert(kCoreMax * 2 + 32 * ((kCoreMax + 2 + 31) / 32) * 4 <= kArea, "bitset rows fit");
     static_assert((kCoreMax * 2) % 16 == 0 && kMarkStride % 16 == 0, "byte rows are 16-byte aligned");
     constexpr int kWordsPerThread = (kCoreMax / 32 + kWarps - 1) / kWarps;
-    const uint32_t *bits = reinterpret_cast<const uint32_t *>(p.wl[1]);
     const int Hp = (H + 31) & ~31;  // column stride of the bit matrix
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 32 * kMarkStride / 4; i += kBlock) reinterpret_cast<uint32_t *>(mark)[i] = 0u;
@@ -2016,7 +2012,7 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
     int32_t vid = -1;
     if (wid == 0 && lane < min(32, H)) {
         inb = __ldcg(bits + lane);  // word 0 of rank lane
-        vid = __ldcg(p.mid_all + lane);
+        vid = __ldcg(list + lane);
     }
     __syncthreads();
     for (int b = 0; 32 * b < H; ++b) {
@@ -2102,7 +2098,7 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
             const int bm = __reduce_max_sync(FULL_MASK, mine);
             // the next batch's in-batch word and vertices
             inb = r1 < H ? __ldcg(bits + (size_t)b1 * Hp + r1) : 0u;
-            vid = r1 < H ? __ldcg(p.mid_all + r1) : -1;
+            vid = r1 < H ? __ldcg(list + r1) : -1;
             if (lane == 0) sh.claim = max(M, bm);
         }
         __syncthreads();
@@ -2123,69 +2119,119 @@ __device__ __noinline__ int core_colour(const KParams &p, Shared &sh, int H, int
 }
 
 
-// The core phase of the asynchronous mode of one graph (all blocks; block 0
-// has just run plan_ordering): the hubs of degree > core_deg are listed; if
-// there are 1..kCoreMax of them and their bit matrix fits, block 0 sorts them
-// while the other blocks clear the matrix, then all build it, then block 0
-// colours the core (the hub pass then skips them); else they stay ordinary
-// hubs.  Ends with a grid barrier either way; st->core_n is the core's size
-// (0: none).
+// The core phase of the asynchronous mode (all blocks; block 0 has just run
+// plan_ordering).  Each graph's hubs of degree > core_deg are counted; a
+// graph with 1..kCoreMax of them whose bit matrix still fits the buffer gets
+// a core: its candidates are listed, one block sorts them, all blocks build
+// the bit matrices, and one block per graph colours its core (the hub pass
+// then skips them); the others stay ordinary hubs.  Ends with a grid barrier.
+template <bool BATCH>
 __device__ __noinline__ void core_stage(const KParams &p, Shared &sh)
 {
     DevState *st = p.st;
     const unsigned nbl = gridDim.x;
+    const int lane = threadIdx.x & 31;
     const bool snap = (p.mode & GC_REPAIR_SNAPSHOT) && !(p.mode & GC_ALG_TWO_PHASE);
     long long mb = 0;
-    int core_n = 0;
-    // the candidates: hubs of degree > core_deg, listed in p.mid_all
     const int nh = ld_volatile(&st->hub_all_count);
-    for (int i0 = blockIdx.x * kBlock; i0 < nh; i0 += nbl * kBlock) {
-        const int i = i0 + threadIdx.x;
-        bool cand = false;
-        int32_t v = 0;
-        if (i < nh) {
-            v = __ldcg(p.hub_all + i);
-            cand = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v) > p.core_deg;
-        }
-        const unsigned m = __ballot_sync(FULL_MASK, cand);
-        if (m) {
-            const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-            int ob = 0;
-            if (lane == leader) ob = atomicAdd(&st->core_count, __popc(m));
-            ob = __shfl_sync(FULL_MASK, ob, leader);
-            if (cand) __stcg(p.mid_all + ob + __popc(m & ((1u << lane) - 1u)), v);
-        }
+    // each graph's candidates
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < nh; i += nbl * kBlock) {
+        const int32_t v = __ldcg(p.hub_all + i);
+        int64_t beg, end;
+        int32_t nbase, g;
+        row_of<BATCH>(p, v, beg, end, nbase, g);
+        if (end - beg > p.core_deg) atomicAdd(&p.gstat[g].core_cnt, 1);
     }
     grid_sync(st, nbl);
-    const int H = ld_volatile(&st->core_count);
-    const int W = (H + 31) / 32;
-    // more than kCoreMax, or a bit matrix larger than a worklist buffer: no
-    // core (the candidates stay ordinary hubs)
-    if (H > 0 && H <= kCoreMax && (long long)32 * W * W <= (long long)p.n) {
-        core_n = H;
-        if (blockIdx.x == 0) core_sort(p, sh, H);
-        if (nbl == 1 || blockIdx.x > 0) {
-            const long long words = (long long)32 * W * W;
-            const long long nclr = nbl > 1 ? (long long)(nbl - 1) * kBlock : kBlock;
-            const long long first = (long long)(nbl > 1 ? blockIdx.x - 1 : 0) * kBlock + threadIdx.x;
-            for (long long i = first; i < words; i += nclr) __stcg(p.wl[1] + i, 0);
+    // block 0: which graphs get a core (those with 1..kCoreMax candidates, in
+    // graph order while their lists and bit matrices fit: the prefix sums
+    // only grow, so the graphs with a core come before the first that does
+    // not fit), their list offsets and bit-matrix words
+    if (blockIdx.x == 0) {
+        long long carry_c = 0, carry_w = 0;
+        for (int g0 = 0; g0 < p.G; g0 += kBlock) {
+            const int g = g0 + threadIdx.x;
+            int H = 0;
+            if (g < p.G) {
+                H = __ldcg(&p.gstat[g].core_cnt);
+                if (H > kCoreMax) H = 0;
+            }
+            const int W = (H + 31) / 32;
+            int tot_c, tot_w;
+            const int before_c = block_exclusive_scan(H, reinterpret_cast<int *>(sh.warp_bm), tot_c);
+            const int before_w = block_exclusive_scan(W * W, reinterpret_cast<int *>(sh.warp_bm), tot_w);
+            if (g < p.G) {
+                const long long off = carry_c + before_c, bofs = carry_w + 32ll * before_w;
+                const bool on = H > 0 && off + H < (long long)p.n && bofs + 32ll * W * W <= (long long)p.n;
+                p.gstat[g].core_on = on;
+                p.gstat[g].core_off = (int)off;
+                p.gstat[g].core_bofs = (int)bofs;
+                p.gstat[g].core_cnt = on ? H : 0;
+                if (on) {
+                    atomicMax(&st->core_count, (int)(off + H));          // entries listed
+                    atomicMax(&st->core_words, bofs + 32ll * W * W);     // words to clear
+                }
+            }
+            carry_c += tot_c;
+            carry_w += 32ll * tot_w;
+        }
+        __syncthreads();
+    }
+    grid_sync(st, nbl);
+    // the candidates of the graphs with a core, listed graph by graph; their
+    // bit matrices cleared
+    const long long words_all = *(volatile long long *)&st->core_words;
+    const int T = ld_volatile(&st->core_count);
+    for (int i = blockIdx.x * kBlock + threadIdx.x; i < nh; i += nbl * kBlock) {
+        const int32_t v = __ldcg(p.hub_all + i);
+        int64_t beg, end;
+        int32_t nbase, g;
+        row_of<BATCH>(p, v, beg, end, nbase, g);
+        if (end - beg > p.core_deg && __ldcg(&p.gstat[g].core_on)) {
+            const int o = __ldcg(&p.gstat[g].core_off) + atomicAdd(&p.gstat[g].core_fill, 1);
+            __stcg(p.mid_all + o, v);
+            if (BATCH) __stcg(p.hub[0] + o, g);
         }
     }
-    grid_sync(st, nbl, kBarrierTimeoutNs, core_n > 0 ? 512 : 64);
-    if (core_n > 0 && ld_volatile(&st->error) == 0) {
-        core_build(p, core_n, mb);
+    for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < words_all; i += (long long)nbl * kBlock)
+        __stcg(p.wl[1] + i, 0);
+    grid_sync(st, nbl);
+    // one block per core: sort, rank marks, task counts
+    for (;;) {
+        if (threadIdx.x == 0) sh.claim = atomicAdd(&st->core_n, 1);
+        __syncthreads();
+        const int g = sh.claim;
+        __syncthreads();
+        if (g >= p.G) break;
+        const int H = __ldcg(&p.gstat[g].core_cnt);
+        if (H == 0) continue;
+        const int off = __ldcg(&p.gstat[g].core_off);
+        core_sort<BATCH>(p, sh, p.mid_all + off, H, p.hub[1] + off);
+    }
+    grid_sync(st, nbl);
+    if (T > 0) {
+        if (blockIdx.x == 0) block_scan_inplace(p.hub[1], T, sh);
         grid_sync(st, nbl);
-        if (blockIdx.x == 0) {
-            const int M = core_colour(p, sh, core_n, snap ? p.cB : nullptr);
-            if (threadIdx.x == 0) {
-                st->core_n = core_n;
-                st->core_colors = M;
-            }
+        core_build<BATCH>(p, T, mb);
+        grid_sync(st, nbl);
+        // one block per core: colour it
+        for (;;) {
+            if (threadIdx.x == 0) sh.claim = atomicAdd(&st->core_colors, 1);
+            __syncthreads();
+            const int g = sh.claim;
+            __syncthreads();
+            if (g >= p.G) break;
+            const GraphStat &gs = p.gstat[g];
+            const int H = __ldcg(&gs.core_cnt);
+            if (H == 0) continue;
+            core_colour(p, sh, p.mid_all + __ldcg(&gs.core_off),
+                        reinterpret_cast<const uint32_t *>(p.wl[1]) + __ldcg(&gs.core_bofs), H,
+                        snap ? p.cB : nullptr);
         }
-        grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for block 0's serial work
+        grid_sync(st, nbl, kBarrierTimeoutNs, 1024);  // the grid waits for the cores' serial work
     }
     for (int o = 16; o > 0; o >>= 1) mb += __shfl_down_sync(FULL_MASK, mb, o);
-    if ((threadIdx.x & 31) == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
+    if (lane == 0 && mb) atomicAdd(&st->model_bytes, (unsigned long long)mb);
 }
 
 // The prologue of a colouring launch (all blocks): degree binning of V (hub lists),
@@ -2404,8 +2450,8 @@ __device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
             // The core of one graph (see core_sort); its first barrier also
             // ends plan_ordering.
-            if (!BATCH && p.core_deg > 0 && ld_volatile(&st->hub_all_count) > 0)
-                core_stage(p, sh);
+            if (p.core_deg > 0 && ld_volatile(&st->hub_all_count) > 0)
+                core_stage<BATCH>(p, sh);
             else
                 grid_sync(st, nbl);
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);

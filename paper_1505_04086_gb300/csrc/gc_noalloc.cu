@@ -184,7 +184,7 @@ extern "C" int gc_color_noalloc(const gc_csr *csr, int32_t n, int64_t nnz, uint3
     p.tile = tile;
     p.tail = tail;
     p.window = o.window;
-    p.core_deg = gc::core_applies(mode, false, false) ? (o.core_deg > 0 ? o.core_deg : (o.core_deg < 0 ? 0 : gc::kCoreDeg))
+    p.core_deg = gc::core_applies(mode, false) ? (o.core_deg > 0 ? o.core_deg : (o.core_deg < 0 ? 0 : gc::kCoreDeg))
                                                       : 0;
 
     const bool async = (mode & GC_SCHED_ASYNC) != 0;

@@ -124,3 +124,43 @@ def test_core_noalloc_matches(ctx):
     assert O.check(g, c)[0] == 0
     order = core_order(g, 128)
     assert np.array_equal(c[order], O.ff(induced(g, order)))
+
+
+def _batch_run(ctx, gs, mode, opts=None):
+    b = I.Batch.from_graphs(gs, name="t")
+    d = torch.device("cuda:0")
+    vo, eo = torch.from_numpy(b.vtx_off).to(d), torch.from_numpy(b.edge_off).to(d)
+    rp, ci = torch.from_numpy(b.row_ptr).to(d), torch.from_numpy(b.col_idx).to(d)
+    col = torch.empty(b.total_n, dtype=torch.int32, device=d)
+    rc = gc.gc_color_batch(ctx.handle, b.G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, None, None, opts)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    rc, st = gc.gc_ctx_stats(ctx.handle)
+    assert rc == gc.GC_OK, gc.gc_strerror(rc)
+    c = col.cpu().numpy()
+    return [c[int(b.vtx_off[i]):int(b.vtx_off[i + 1])] for i in range(b.G)]
+
+
+@pytest.mark.parametrize("mode", ["rsoc", "twophase"])
+def test_batch_cores_are_sequential_first_fit(ctx, mode):
+    # every graph of a batch gets its own core
+    thr = 256
+    gs = [I.rmat(14, 16, seed=I.SEED_RMAT), I.tri2d(40, 40, 0.2), I.rmat(16, 16, seed=I.SEED_RMAT + 7),
+          I.rgg(5000, seed=11), I.rmat(15, 16, seed=I.SEED_RMAT + 3)]
+    cols = _batch_run(ctx, gs, MODES[mode] | gc.GC_CHECKED, {"t1": 16, "t2": thr, "core_deg": thr})
+    for g, c in zip(gs, cols):
+        assert O.check(g, c)[0] == 0, g.name
+        order = core_order(g, thr)
+        if 0 < len(order) <= 4096:
+            assert np.array_equal(c[order], O.ff(induced(g, order))), g.name
+
+
+def test_batch_rmat18_requests_within_bound(ctx):
+    # the serving mix: R-MAT 2^18 graphs among meshes, default options
+    mix = I.batch(12, seed=I.SEED_SERVE)
+    gs = [mix.graph(i) for i in range(mix.G)] + [I.rmat(18, 16, seed=I.SEED_SERVE + 100 + k) for k in range(2)]
+    for mode in (ASYNC, ASYNC | TWOP):
+        cols = _batch_run(ctx, gs, mode | gc.GC_CHECKED)
+        for g, c in zip(gs, cols):
+            bad, mx, _ = O.check(g, c)
+            assert bad == 0
+            assert mx <= 1.1 * int(O.ff(g).max()), (g.name, mx)
