@@ -57,6 +57,8 @@ def parse():
                     help="single graph: headline options as JSON (gc_opts fields) instead of the autotuner's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline mode only")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="default workload: skip the R-MAT 2^22, batch and serving records")
     return ap.parse_args()
 
 
@@ -409,13 +411,13 @@ def run_ours(args, ws, rank, local):
     ff_colors = None
     cpu_omp = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu, ff_colors = cpu_baseline(g, budget_s=12.0)
+        cpu, ff_colors = cpu_baseline(g)
         cpu_omp = host_openmp(gc, g)
 
     if ff_colors:
         for v in extra.values():
             v["colors_vs_ff"] = round(v["colors"] / ff_colors, 4)
-    launches_per_call = 1  # color_kernel (colour statistics at its end)
+    launches_per_call = 2  # prologue_kernel + color_kernel (colour statistics at its end)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -438,6 +440,29 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches_per_call * args.steps, "clocks": clocks, "modes": extra,
         "wall_s": round(wall, 3),
     }
+    if ws == 1 and not args.no_extra and not args.no_nested:
+        # The other configurations, each a complete record of its own:
+        # R-MAT 2^22 (c2), the 4096-graph batch (c3), serving (c4).
+        del rp, ci, res, col_chk, h_rp, h_ci, h_col
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        g2 = I.workload("rmat22_ef16")
+        line["c2"] = single_record(ctx, gc, torch, g2, dev, flush, stream, peak, peak_kind, max(3, min(args.steps, 20)),
+                                   max(3, args.warmup), o2_graph=I.rmat(18, 16))
+        line["c2"]["wall_s"] = round(time.perf_counter() - t0, 1)
+        del g2
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        b = I.batch(BATCH_G, seed=I.SEED_BATCH)
+        line["c3"], _, _ = batch_record(b, BATCH_G, "rsoc_async", max(3, min(args.steps, 20)), max(3, args.warmup), 1,
+                                        dev, ctx, gc, torch, flush, stream)
+        line["c3"]["wall_s"] = round(time.perf_counter() - t0, 1)
+        del b
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        line["c4"] = serve_record(local, "rsoc_async", 10000)
+        line["c4"]["wall_s"] = round(time.perf_counter() - t0, 1)
     ctx.close()
     if ws > 1:
         import torch.distributed as dist
@@ -484,24 +509,130 @@ def host_openmp(gc, g, runs=3):
     return out
 
 
-def cpu_baseline(g, budget_s=12.0):
-    """The oracle's Algorithm 3 replay (single-threaded C) on the same graph,
-    repeated until ~budget_s of CPU time; also the colour count of the
-    oracle's sequential First-Fit (Algorithm 1), the quality reference."""
-    import oracle
-    ff_colors = int(oracle.ff(g).max())
-    runs, t_all = 0, 0.0
-    while t_all < budget_s or runs == 0:
+def median_time(fn, runs=5, warm=1):
+    """Median wall time (s) of `runs` calls of fn after `warm` untimed ones;
+    also the last result."""
+    out = None
+    for _ in range(warm):
+        out = fn()
+    ts = []
+    for _ in range(runs):
         t0 = time.perf_counter()
-        oracle.rsoc_det(g)
-        t_all += time.perf_counter() - t0
-        runs += 1
-        if runs >= 20:
-            break
-    per = t_all / runs
-    return ({"value": round(g.num_edges / per, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
-             "sample": f"oracle.rsoc_det (Algorithm 3 snapshot replay, C, 1 thread) on the full "
-                       f"{g.name} graph x {runs} runs, {per:.3f} s each"}, ff_colors)
+        out = fn()
+        ts.append(time.perf_counter() - t0)
+    return float(np.median(ts)), out
+
+
+def cpu_baseline(g, o2_graph=None, runs=5):
+    """The oracle as it stands, single-threaded C on one host core: its
+    Algorithm 3 replay (O-2; the line's value, edges/s) and its sequential
+    First-Fit (O-1, Algorithm 1; also the colour count the 1.1x bound refers
+    to), each the median of `runs` runs after one warm-up.  O-2 runs on
+    `o2_graph` (a smaller graph from the same generator) where the full graph
+    would take minutes; O-1 always on the full graph."""
+    import oracle
+    t_ff, ff = median_time(lambda: oracle.ff(g), runs)
+    ff_colors = int(ff.max()) if g.n else 0
+    s = o2_graph if o2_graph is not None else g
+    t_o2, _ = median_time(lambda: oracle.rsoc_det(s), runs)
+    where = f"the full {g.name} graph" if s is g else f"{s.name} ({s.n} vertices; bounded sample of {g.name})"
+    return ({"value": round(s.num_edges / t_o2, 1), "unit": "edges/s", "cores": 1, "kind": "oracle",
+             "sample": f"oracle.rsoc_det (Algorithm 3 snapshot replay, C, 1 thread) on {where}, "
+                       f"median of {runs} runs after 1 warm-up",
+             "o2_ms": round(t_o2 * 1e3, 2),
+             "o1_ff": {"value": round(g.num_edges / t_ff, 1), "unit": "edges/s", "ms": round(t_ff * 1e3, 2),
+                       "colors": ff_colors,
+                       "sample": f"oracle.ff (Algorithm 1, sequential First-Fit, C, 1 thread) on the full "
+                                 f"{g.name} graph, median of {runs} runs after 1 warm-up"}},
+            ff_colors)
+
+
+def mode_summary(r, E, peak, ff_colors):
+    """Timing and quality summary of one time_mode result."""
+    tm = float(np.mean(r["step_ms"]))
+    out = {"value": round(E / (tm / 1e3), 1), "ms_per_step": round(tm, 4),
+           "p50_ms": round(pct(r["step_ms"], 50), 4), "p99_ms": round(pct(r["step_ms"], 99), 4),
+           "rounds": int(np.median(r["rounds"])), "conflicts": int(np.median(r["conflicts"])),
+           "colors": int(np.max(r["colors"])),
+           "kernel_frac": round(np.mean(r["model_bytes"]) / (np.mean(r["kern_ms"]) / 1e3) / 1e9 / peak, 4),
+           "steps": len(r["step_ms"])}
+    if ff_colors:
+        out["colors_vs_ff"] = round(out["colors"] / ff_colors, 4)
+    return out
+
+
+def single_record(ctx, gc, torch, g, dev, flush, stream, peak, peak_kind, steps, warmup, o2_graph=None,
+                  extra_modes=("twophase_async", "rsoc_det", "twophase_det"), det_steps=5):
+    """A complete record for one single-graph workload (used for R-MAT
+    2^22): asynchronous RSOC with autotuned options as its value (edges/s,
+    graph resident, L2 flushed before every step), the kernel's roofline,
+    the other modes, colours against sequential First-Fit, end to end
+    through gc_color with pinned host buffers, and the CPU oracle."""
+    head = "rsoc_async"
+    E = g.num_edges
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    col = torch.empty(g.n, dtype=torch.int32, device=dev)
+    t_tune = time.perf_counter()
+    rc, tune = gc.gc_autotune(ctx.handle, rp, ci, g.n, g.nnz, MODES[head], col, reps=3)
+    if rc != gc.GC_OK:
+        raise RuntimeError(gc.gc_strerror(rc))
+    t_tune = time.perf_counter() - t_tune
+    opts = tune["best"]
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    time.sleep(0.15)
+    res = time_mode(ctx, gc, torch, rp, ci, g, MODES[head], steps, warmup, flush, stream, opts)
+    clocks = sampler.stop()
+    rc = gc.gc_color_async(ctx.handle, rp, ci, g.n, g.nnz, MODES[head] | gc.GC_CHECKED, col, opts, stream)
+    rc2, _ = gc.gc_ctx_stats(ctx.handle)
+    if rc != gc.GC_OK or rc2 != gc.GC_OK:
+        raise RuntimeError(f"device check of the colouring failed: {gc.gc_strerror(rc2)}")
+    mb = float(np.mean(res["model_bytes"]))
+    kms = float(np.mean(res["kern_ms"]))
+    achieved = mb / (kms / 1e3) / 1e9
+    modes = {}
+    for name in extra_modes:
+        k = det_steps if not (MODES[name] & gc.GC_SCHED_ASYNC) else max(3, min(steps, 20))
+        modes[name] = time_mode(ctx, gc, torch, rp, ci, g, MODES[name], k, 1 if k == det_steps else 3, flush,
+                                stream)
+    del rp, ci, col
+    # end to end: CSR up from pinned host memory, colours back, every step
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    h_col = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    for _ in range(3):
+        gc.gc_color(h_rp, h_ci, g.n, g.nnz, MODES[head], h_col)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(3, min(steps, 20))):
+        t1 = time.perf_counter()
+        rc, _ = gc.gc_color(h_rp, h_ci, g.n, g.nnz, MODES[head], h_col)
+        times.append(time.perf_counter() - t1)
+        if rc != gc.GC_OK:
+            raise RuntimeError(gc.gc_strerror(rc))
+    e2e = {"value": round(E * len(times) / sum(times), 1), "unit": "edges/s",
+           "h2d_bytes_per_step": int(h_rp.numel() * 4 + h_ci.numel() * 4),
+           "d2h_bytes_per_step": int(h_col.numel() * 4), "p50_ms": round(1e3 * float(np.median(times)), 4),
+           "steps": len(times), "api": "gc_color (host pointers, pinned)"}
+    cpu, ff_colors = cpu_baseline(g, o2_graph)
+    head_sum = mode_summary(res, E, peak, ff_colors)
+    return {"workload": g.name, "n": g.n, "edges": E, "nnz": g.nnz, "mode": head,
+            "metric": METRIC, "unit": "edges/s", "value": head_sum["value"],
+            "ms_per_step": head_sum["ms_per_step"], "p50_ms": head_sum["p50_ms"], "p99_ms": head_sum["p99_ms"],
+            "steps": steps, "warmup": warmup, "colors": head_sum["colors"], "seq_ff_colors": ff_colors,
+            "colors_vs_ff": head_sum.get("colors_vs_ff"), "colors_runs": [int(x) for x in res["colors"]],
+            "rounds": head_sum["rounds"], "conflicts": head_sum["conflicts"],
+            "l2": "flushed between steps (512 MB write)",
+            "autotune": {"opts": opts, "best_ms": round(tune["best_ms"], 4), "default_ms": round(tune["default_ms"], 4),
+                         "evaluated": tune["evaluated"], "seconds": round(t_tune, 2)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
+                         "traffic": recorded_traffic(g.name.replace("_perm", ""), head),
+                         "kernel": "gc::color_kernel<async>", "algorithmic_bytes_per_launch": int(mb),
+                         "kernel_ms": round(kms, 5)},
+            "modes": {k: mode_summary(v, E, peak, ff_colors) for k, v in modes.items()},
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * steps}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -555,25 +686,32 @@ def run_reference(args, ws, rank):
 BATCH_G = 4096
 
 
-def run_batch(args, ws, rank, local):
+def batch_cpu_baseline(b, sample=32, runs=5, seed=1505):
+    """The oracle on a bounded sample of the batch's graphs, one by one:
+    Algorithm 3 replay (O-2) and sequential First-Fit (O-1), median of
+    `runs` passes over the sample after one warm-up; graphs/s and edges/s."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    ids = sorted(rng.choice(b.G, size=min(sample, b.G), replace=False).tolist())
+    subs = [b.graph(g) for g in ids]
+    E = sum(x.num_edges for x in subs)
+    t2, _ = median_time(lambda: [oracle.rsoc_det(x) for x in subs], runs)
+    t1, _ = median_time(lambda: [oracle.ff(x) for x in subs], runs)
+    return {"value": round(len(subs) / t2, 1), "unit": "graphs/s", "edges_per_s": round(E / t2, 1), "cores": 1,
+            "kind": "oracle",
+            "sample": f"oracle.rsoc_det (Algorithm 3 snapshot replay, C, 1 thread) on {len(subs)} graphs drawn "
+                      f"from the batch ({E} edges), median of {runs} passes after 1 warm-up",
+            "o1_ff": {"value": round(len(subs) / t1, 1), "unit": "graphs/s", "edges_per_s": round(E / t1, 1),
+                      "sample": "oracle.ff (Algorithm 1) on the same graphs, median of 5 passes after 1 warm-up"}}
+
+
+def batch_record(b, graphs_total, mode_name, steps, warmup, ws, dev, ctx, gc, torch, flush, stream, tune=True,
+                 cpu=True):
     """Many uneven graphs in one persistent launch, against one plain launch
-    per graph.  The options (bin thresholds, tile, blocks per SM, tail,
-    ordering) come from the library's autotuner, run on the batch before the
+    per graph.  Options from the library's autotuner, chosen before the
     timed region; each timed step replays the batch colouring captured in a
-    CUDA graph (gc_plan_launch).  Every rank colours its own share of the
-    graphs (sharded by size, no collective)."""
-    import torch
-    from paper_1505_04086_gb300 import gc
+    CUDA graph (gc_plan_launch).  Returns (record, edges per step, graphs)."""
     from paper_1505_04086_gb300 import dist as D
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    torch.cuda.set_device(local)
-    dev = torch.device(f"cuda:{local}")
-    full = I.batch(args.graphs, seed=I.SEED_BATCH)
-    sizes = np.diff(full.vtx_off)
-    mine = D.shard_graphs(sizes, rank, ws)
-    b = I.Batch.from_graphs([full.graph(g) for g in mine], name="batch") if ws > 1 else full
     G = b.G
     E = b.total_nnz // 2
     vo = torch.from_numpy(b.vtx_off).to(dev)
@@ -583,27 +721,24 @@ def run_batch(args, ws, rank, local):
     col = torch.empty(b.total_n, dtype=torch.int32, device=dev)
     rounds = torch.empty(G, dtype=torch.int32, device=dev)
     confl = torch.empty(G, dtype=torch.int64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    ctx = gc.Context(local)
-    mode_name = args.mode
     mode = MODES[mode_name]
-    steps = max(3, min(args.steps, 20))
+    local = dev.index or 0
     t_tune = time.perf_counter()
-    if args.no_tune:
-        tune = {"best": None, "best_ms": 0.0, "default_ms": 0.0, "evaluated": 0}
+    if not tune:
+        tr = {"best": None, "best_ms": 0.0, "default_ms": 0.0, "evaluated": 0}
     else:
-        rc, tune = gc.gc_autotune_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, reps=1)
+        rc, tr = gc.gc_autotune_batch(ctx.handle, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, reps=1)
         if rc != gc.GC_OK:
             raise RuntimeError(gc.gc_strerror(rc))
     t_tune = time.perf_counter() - t_tune
-    opts = tune["best"]
+    opts = tr["best"]
     plan = gc.Plan(local, G, b.total_n, b.total_nnz, vo, eo, rp, ci, mode, col, rounds, confl, opts=opts)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         assert plan.launch(stream) == gc.GC_OK
         assert plan.stats()[0] == gc.GC_OK
     sampler = ClockSampler(local)
     sampler.start()
+    time.sleep(0.15)
     ms, kms, mbs = [], [], []
     for _ in range(steps):
         flush.zero_()
@@ -629,7 +764,24 @@ def run_batch(args, ws, rank, local):
     rc2, _ = gc.gc_ctx_stats(ctx.handle)
     if rc != gc.GC_OK or rc2 != gc.GC_OK:
         raise RuntimeError(f"device check of the batch colouring failed: {gc.gc_strerror(rc2)}")
-    # per-graph plain launches, same graphs, same mode (one pass)
+    # colours of a sample of the graphs against the oracle's sequential First-Fit
+    import oracle
+    qrng = np.random.default_rng(2024)
+    qids = sorted(qrng.choice(G, size=min(64, G), replace=False).tolist())
+    hcol = col.cpu().numpy()
+    qr = []
+    for gi in qids:
+        sub = b.graph(gi)
+        if sub.n:
+            ff = int(oracle.ff(sub).max())
+            qr.append(int(hcol[int(b.vtx_off[gi]):int(b.vtx_off[gi + 1])].max()) / ff)
+    quality = {"graphs_checked": len(qr), "worst_colors_vs_ff": round(max(qr), 4) if qr else None,
+               "over_1.1": int(sum(r > 1.1 for r in qr))}
+    del hcol
+    plan.close()
+    del vo, eo, rp, ci, rounds, confl
+    # per-graph plain launches, same graphs, same mode (one pass, each graph
+    # resident before the timed loop)
     subs = []
     for g in range(G):
         sub = b.graph(g)
@@ -643,29 +795,62 @@ def run_batch(args, ws, rank, local):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
     _, plain_s = D.aggregate(0, plain_s, device=dev)
-    line = {"metric": "colored edges/s", "value": round(units / secs, 1), "unit": "edges/s", "n_gpus": ws,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / steps, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-            "data": "synthetic (seeded generator)",
-            "config": {"workload": f"batch{args.graphs}_mesh_rgg_1k_256k", "graphs": args.graphs,
-                       "n": int(full.total_n), "edges": int(full.total_nnz // 2), "mode": mode_name,
-                       "l2": "flushed between steps (512 MB write)", "parallelism": f"graph-shards{ws}",
-                       "launch": "CUDA graph replay (gc_plan_launch)"},
-            "graphs_per_s": round(gunits / secs, 1),
-            "p50_ms": round(pct(ms, 50), 4), "p99_ms": round(pct(ms, 99), 4),
-            "plain_launches_graphs_per_s": round(ws * G / plain_s, 1),
-            "speedup_vs_plain": round((gunits / secs) / (ws * G / plain_s), 2),
-        "autotune": {"opts": opts, "best_ms": round(tune["best_ms"], 3),
-                         "default_ms": round(tune["default_ms"], 3), "evaluated": tune["evaluated"],
-                         "seconds": round(t_tune, 1)},
-            "rounds": st["rounds"], "conflicts": st["conflicts"],
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
-                         "traffic": recorded_traffic(f"batch{args.graphs}", mode_name),
-                         "kernel": "gc::color_kernel<async,batch>",
-                         "algorithmic_bytes_per_launch": int(np.mean(mbs)), "kernel_ms": round(float(np.mean(kms)), 4)},
-            "gpu_launches": 2 * steps, "clocks": clocks}  # lut, colour
-    plan.close()
+    del subs, col
+    rec = {"workload": f"batch{graphs_total}_mesh_rgg_1k_256k", "graphs": graphs_total, "graphs_this_rank": G,
+           "n": int(b.total_n), "edges": int(E), "mode": mode_name, "metric": METRIC, "unit": "edges/s",
+           "value": round(units / secs, 1), "ms_per_step": round(secs * 1e3 / steps, 4), "steps": steps,
+           "l2": "flushed between steps (512 MB write)", "launch": "CUDA graph replay (gc_plan_launch)",
+           "graphs_per_s": round(gunits / secs, 1),
+           "p50_ms": round(pct(ms, 50), 4), "p99_ms": round(pct(ms, 99), 4),
+           "plain_launches_graphs_per_s": round(ws * G / plain_s, 1),
+           "speedup_vs_plain": round((gunits / secs) / (ws * G / plain_s), 2),
+           "autotune": {"opts": opts, "best_ms": round(tr["best_ms"], 3), "default_ms": round(tr["default_ms"], 3),
+                        "evaluated": tr["evaluated"], "seconds": round(t_tune, 1)},
+           "rounds": st["rounds"], "conflicts": st["conflicts"], "colors_vs_ff": quality,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
+                        "traffic": recorded_traffic(f"batch{graphs_total}", mode_name),
+                        "kernel": "gc::color_kernel<async,batch>",
+                        "algorithmic_bytes_per_launch": int(np.mean(mbs)),
+                        "kernel_ms": round(float(np.mean(kms)), 4)},
+           "gpu_launches": 3 * steps, "clocks": clocks}  # lut, prologue, colour
+    if cpu:
+        rec["cpu_baseline"] = batch_cpu_baseline(b)
+    return rec, units, secs
+
+
+def run_batch(args, ws, rank, local):
+    """The batch workload on its own line: every rank colours its own share
+    of the graphs (sharded by size, no collective)."""
+    import torch
+    from paper_1505_04086_gb300 import gc
+    from paper_1505_04086_gb300 import dist as D
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    full = I.batch(args.graphs, seed=I.SEED_BATCH)
+    sizes = np.diff(full.vtx_off)
+    mine = D.shard_graphs(sizes, rank, ws)
+    b = I.Batch.from_graphs([full.graph(g) for g in mine], name="batch") if ws > 1 else full
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gc.Context(local)
+    steps = max(3, min(args.steps, 20))
+    rec, units, secs = batch_record(b, args.graphs, args.mode, steps, args.warmup, ws, dev, ctx, gc, torch, flush,
+                                    stream, tune=not args.no_tune, cpu=(rank == 0 and ws == 1 and
+                                                                        not args.no_cpu_baseline))
+    line = {"metric": METRIC, "value": rec["value"], "unit": "edges/s", "n_gpus": ws, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generator)",
+            "config": {"workload": rec["workload"], "graphs": args.graphs, "n": int(full.total_n),
+                       "edges": int(full.total_nnz // 2), "mode": args.mode, "l2": rec["l2"],
+                       "parallelism": f"graph-shards{ws}", "launch": rec["launch"]}}
+    for k in ("graphs_per_s", "p50_ms", "p99_ms", "plain_launches_graphs_per_s", "speedup_vs_plain", "autotune",
+              "rounds", "conflicts", "colors_vs_ff", "roofline", "gpu_launches", "clocks", "cpu_baseline"):
+        if k in rec:
+            line[k] = rec[k]
     ctx.close()
     if ws > 1:
         import torch.distributed as dist
@@ -682,21 +867,24 @@ def serve_pool(seed=I.SEED_SERVE, n_mix=256, n_rmat=8):
     return pool, rm
 
 
-def run_serve(args, ws, rank, local):
+def serve_record(local, mode_name, nreq=10000):
     """Poisson arrivals of colouring requests (95% from the batch size mix,
     5% R-MAT scale 18) served with continuous batching under a fixed
-    device-memory budget, against plain per-request launches."""
+    device-memory budget, against plain per-request launches (gc_color on
+    the same host arrays, one request at a time).  Saturation throughput,
+    then 0.5 / 0.8 / 0.95 of it with p50/p99 latency (submit to result)."""
     import threading
     import torch
     from paper_1505_04086_gb300 import gc
     torch.cuda.set_device(local)
     pool, rm = serve_pool()
     rng = np.random.default_rng(7)
-    nreq = max(200, min(args.steps * 50, 4000))
     picks = [(rm[int(rng.integers(len(rm)))] if rng.random() < 0.05 else pool[int(rng.integers(len(pool)))])
              for _ in range(nreq)]
     budget = 8 << 30
-    mode = MODES[args.mode]
+    mode = MODES[mode_name]
+
+    kcol = [0] * nreq  # colours of each request's result
 
     def serve(rate):
         srv = gc.Server(local, budget_bytes=budget, max_slots=1024, mode=mode)
@@ -712,6 +900,7 @@ def run_serve(args, ws, rank, local):
                 if rc != gc.GC_OK:
                     raise RuntimeError(gc.gc_strerror(rc))
                 lat[i] = st["elapsed_ms"]
+                kcol[i] = st["colors"]
         th = threading.Thread(target=collector)
         th.start()
         t0 = time.perf_counter()
@@ -751,6 +940,23 @@ def run_serve(args, ws, rank, local):
         return nreq / wall, float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
 
     sat, _, _, _ = serve(0)            # everything at once: saturation throughput
+    # colours of every request of that run against the oracle's sequential
+    # First-Fit of its graph (one CPU run per distinct graph)
+    import oracle
+    ff_of = {}
+    ratios, rm_ratios = [], []
+    for i, g in enumerate(picks):
+        key = id(g)
+        if key not in ff_of:
+            ff_of[key] = int(oracle.ff(g).max()) if g.n else 0
+        if ff_of[key]:
+            r = kcol[i] / ff_of[key]
+            ratios.append(r)
+            if g.name.startswith("rmat"):
+                rm_ratios.append(r)
+    quality = {"requests": len(ratios), "worst_colors_vs_ff": round(max(ratios), 4),
+               "over_1.1": int(sum(r > 1.1 for r in ratios)),
+               "rmat18_requests": len(rm_ratios), "rmat18_worst_colors_vs_ff": round(max(rm_ratios), 4) if rm_ratios else None}
     plain_sat, _, _ = plain(0)
     levels = {}
     for f in (0.5, 0.8, 0.95):
@@ -759,15 +965,25 @@ def run_serve(args, ws, rank, local):
                           "p50_ms": round(p50, 3), "p99_ms": round(p99, 3), "waves": info["waves"],
                           "peak_bytes": info["peak_bytes"], "max_wave_graphs": info["max_wave_graphs"]}
     thr, p50, p99 = plain(0.8 * plain_sat)
-    line = {"metric": "graphs/s", "value": round(sat, 1), "unit": "graphs/s", "n_gpus": 1, "steps": nreq,
-            "warmup": 0, "ms_per_step": round(1e3 / sat, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generator)",
-            "config": {"workload": "serve_poisson_mix_rmat18", "requests": nreq, "budget_bytes": budget,
-                       "mode": args.mode, "pool": f"{len(pool)} mix graphs + {len(rm)} rmat18"},
-            "plain_launches_graphs_per_s": round(plain_sat, 1),
-            "speedup_vs_plain": round(sat / plain_sat, 2),
-            "load_levels": levels,
+    return {"workload": "serve_poisson_mix_rmat18", "metric": "graphs/s", "unit": "graphs/s",
+            "value": round(sat, 1), "requests": nreq, "budget_bytes": budget, "mode": mode_name,
+            "pool": f"{len(pool)} mix graphs + {len(rm)} rmat18",
+            "plain_launches_graphs_per_s": round(plain_sat, 1), "speedup_vs_plain": round(sat / plain_sat, 2),
+            "colors_vs_ff": quality, "load_levels": levels,
             "plain_at_0.8": {"graphs_per_s": round(thr, 1), "p50_ms": round(p50, 3), "p99_ms": round(p99, 3)}}
+
+
+def run_serve(args, ws, rank, local):
+    """The serving workload on its own line (rank 0 only)."""
+    nreq = max(200, min(args.steps * 500, 10000))
+    rec = serve_record(local, args.mode, nreq)
+    line = {"metric": "graphs/s", "value": rec["value"], "unit": "graphs/s", "n_gpus": 1, "steps": nreq,
+            "warmup": 0, "ms_per_step": round(1e3 / rec["value"], 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded generator)",
+            "config": {"workload": rec["workload"], "requests": nreq, "budget_bytes": rec["budget_bytes"],
+                       "mode": args.mode, "pool": rec["pool"]}}
+    for k in ("plain_launches_graphs_per_s", "speedup_vs_plain", "colors_vs_ff", "load_levels", "plain_at_0.8"):
+        line[k] = rec[k]
     if rank == 0:
         print(json.dumps(line), flush=True)
 
