@@ -271,7 +271,7 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
                 "traffic": recorded_traffic(args.workload, head),
-                "kernel": "gc::color_kernel<async>", "algorithmic_bytes_per_launch": int(mb),
+                "kernel": "gc::prologue_kernel<async> + gc::color_kernel<async> (one colouring)", "algorithmic_bytes_per_launch": int(mb),
                 "kernel_ms": round(kms, 5)}
 
     # validity of the headline mode, checked on the device (untimed)
@@ -440,6 +440,8 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches_per_call * args.steps, "clocks": clocks, "modes": extra,
         "wall_s": round(wall, 3),
     }
+    if rank == 0 and not args.no_extra:
+        line["gather_ceiling"] = gather_ceiling(gc, 4 * g.n)
     if ws == 1 and not args.no_extra and not args.no_nested:
         # The other configurations, each a complete record of its own:
         # R-MAT 2^22 (c2), the 4096-graph batch (c3), serving (c4).
@@ -469,6 +471,41 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def gather_ceiling(gc, array_bytes, blocks_per_sm=2):
+    """Random 4-byte gathers per second from an array the size of the
+    colour array (gc_measure_gather_rate): the ceiling of the kernels'
+    neighbour-colour reads, beside the HBM roofline."""
+    out = {"array_bytes": int(array_bytes), "blocks_per_sm": blocks_per_sm, "unit": "G loads/s",
+           "api": "gc_measure_gather_rate"}
+    for kind, dep in (("independent", False), ("dependent", True)):
+        rc, rate = gc.gc_measure_gather_rate(0, int(array_bytes), blocks_per_sm, dep)
+        out[kind] = round(rate, 1) if rc == gc.GC_OK else None
+    return out
+
+
+def run_gather(args, rank):
+    """--workload gather: the gather-rate table (array sizes from L2-resident
+    to far beyond L2, resident blocks per SM, independent and dependent
+    loads), one JSON line."""
+    if rank != 0:
+        return
+    import torch
+    from paper_1505_04086_gb300 import gc
+    torch.cuda.set_device(0)
+    rows = []
+    for mb in (8, 16, 64, 512):
+        for bps in (1, 2, 3, 4, 8):
+            row = {"array_mb": mb, "blocks_per_sm": bps}
+            for kind, dep in (("independent", False), ("dependent", True)):
+                rc, rate = gc.gc_measure_gather_rate(0, mb << 20, bps, dep)
+                if rc != gc.GC_OK:
+                    raise RuntimeError(gc.gc_strerror(rc))
+                row[kind] = round(rate, 1)
+            rows.append(row)
+    print(json.dumps({"metric": "random 4-byte gathers/s", "unit": "G loads/s", "threads_per_block": 256,
+                      "api": "gc_measure_gather_rate", "rows": rows}), flush=True)
 
 
 def host_openmp(gc, g, runs=3):
@@ -629,10 +666,11 @@ def single_record(ctx, gc, torch, g, dev, flush, stream, peak, peak_kind, steps,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
                          "traffic": recorded_traffic(g.name.replace("_perm", ""), head),
-                         "kernel": "gc::color_kernel<async>", "algorithmic_bytes_per_launch": int(mb),
+                         "kernel": "gc::prologue_kernel<async> + gc::color_kernel<async> (one colouring)", "algorithmic_bytes_per_launch": int(mb),
                          "kernel_ms": round(kms, 5)},
             "modes": {k: mode_summary(v, E, peak, ff_colors) for k, v in modes.items()},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * steps}
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * steps,
+            "gather_ceiling": gather_ceiling(gc, 4 * g.n)}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -810,7 +848,7 @@ def batch_record(b, graphs_total, mode_name, steps, warmup, ws, dev, ctx, gc, to
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4), "peak_kind": f"of {peak_kind} (hbm copy)",
                         "traffic": recorded_traffic(f"batch{graphs_total}", mode_name),
-                        "kernel": "gc::color_kernel<async,batch>",
+                        "kernel": "gc::prologue_kernel<async,batch> + gc::color_kernel<async,batch> (one batch)",
                         "algorithmic_bytes_per_launch": int(np.mean(mbs)),
                         "kernel_ms": round(float(np.mean(kms)), 4)},
            "gpu_launches": 3 * steps, "clocks": clocks}  # lut, prologue, colour
@@ -994,7 +1032,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "batch":
+    if args.workload == "gather":
+        run_gather(args, rank)
+    elif args.workload == "batch":
         run_batch(args, ws, rank, local)
     elif args.workload == "serve":
         if rank == 0:

@@ -639,6 +639,27 @@ enum {
  */
 int gc_debug_wait_timeout(int device, int32_t wait, int32_t timeout_ms, int32_t *error_word_out);
 
+/* ---- measurement ------------------------------------------------------- */
+
+/*
+ * Random 4-byte gathers per second from an array of `array_bytes` bytes
+ * (4 KB .. 1 GB, rounded down to a power of two) on `device`: the ceiling
+ * of the colouring kernels' neighbour-colour reads, which are random 4-byte
+ * loads from the colour array (8 MB for 2^21 vertices, resident in L2).
+ * The paper has no counterpart; it serves the roofline analysis only.
+ * One launch of SMs x blocks_per_sm (1..8) blocks of 256 threads after one
+ * warm-up launch, timed with CUDA events.  dependent = 0: every thread
+ * issues independent loads at hashed positions (eight in flight);
+ * dependent = 1: every thread follows a chain in which each loaded value is
+ * the next position (one load in flight), like the kernels' row pointer ->
+ * column index -> colour chains.  The array is allocated, filled on the
+ * device and freed by the call.  Synchronous.  Writes the loads per second
+ * to *gloads_per_s_out (in units of 1e9).  Returns GC_OK, GC_ERR_ARG,
+ * GC_ERR_OOM or GC_ERR_CUDA.
+ */
+int gc_measure_gather_rate(int device, int64_t array_bytes, int32_t blocks_per_sm, int32_t dependent,
+                           double *gloads_per_s_out);
+
 #ifdef __cplusplus
 }
 #endif

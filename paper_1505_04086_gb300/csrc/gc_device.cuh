@@ -123,13 +123,23 @@ static __device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, u
     __shared__ bool last;
     int mx = 0;
     unsigned long long low = 0;  // colours 0..63, OR-reduced per warp
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = __ldcg(c + i);
+    auto note = [&](int x) {
         mx = max(mx, x);
         if (x >= 0 && x < 64) low |= 1ull << x;
         else if (x >= 64 && x < kStatBitmapWords * 32) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+    };
+    // eight independent loads in flight per thread, then the remainder
+    constexpr int kU = 8;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (kU - 1) * stride < n; i += kU * stride) {
+        int x[kU];
+#pragma unroll
+        for (int q = 0; q < kU; ++q) x[q] = __ldcg(c + i + q * stride);
+#pragma unroll
+        for (int q = 0; q < kU; ++q) note(x[q]);
     }
+    for (; i < n; i += stride) note(__ldcg(c + i));
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_down_sync(FULL_MASK, mx, o));
         low |= __shfl_down_sync(FULL_MASK, low, o);

@@ -1667,6 +1667,45 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
                                                           (gs.all_lower > 0 && 2 * gs.near_lower >= gs.all_lower) ||
                                                           (ng <= kOrderedGroup && groupable(g)))));
     };
+    if (p.G == 1) {
+        // One graph: the same decisions as below, by one thread with rolled
+        // loops (the general form's per-graph loops over the candidates are
+        // unrolled: long straight-line code that a single graph does not
+        // need to fetch).
+        if (threadIdx.x == 0) {
+            const long long ng = graph_n(0);
+            const bool ord = is_ordered(0, ng);
+            const long long c = (ng + 31) / 32;
+            int K = 1;
+            if (ord && groupable(0)) {
+                long long cand = max((c + warps - 1) / max(warps, 1ll), (long long)kPipeMinChunks);
+                long long target = cand;
+                for (int i = 0; i < kTargetSteps; ++i) {
+                    target = cand;  // the last candidate if none fits
+                    const bool grp = c > cand;
+                    const long long wg = grp ? min((c + cand - 1) / cand, (long long)kPipeMaxK) : 0;
+                    if (wg <= budget && (grp ? 0 : c) <= cand * (warps - wg)) break;
+                    cand += cand / 10 + 1;
+                }
+                if (c > target) K = (int)min((c + target - 1) / target, (long long)kPipeMaxK);
+            }
+            p.gstat[0].ordered = ord;
+            p.gstat[0].group = K > 1 ? K : 0;
+            const long long uch = ord ? 0 : c;
+            if (ord && K == 1) p.olist[0] = 0;
+            st->n_ordered = (ord && K == 1) ? 1 : 0;
+            st->n_pitems = (ord && K > 1) ? K : 0;
+            p.uofs[0] = 0;
+            p.uofs[1] = uch;
+            st->n_uchunks = uch;
+            sh.claim = (ord && K > 1) ? K : 0;
+        }
+        __syncthreads();
+        const int K = sh.claim;
+        for (int j = threadIdx.x; j < K; j += kBlock) p.pitems[j] = ((long long)j << 10) | (long long)(K - 1);
+        __syncthreads();
+        return;
+    }
     // Ordered chunks in all.
     long long T = 0;
     for (int g0 = 0; g0 < p.G; g0 += kBlock) {
@@ -2263,9 +2302,9 @@ __device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
                 if (keep) p.mark[v] = 0;
             }
         }
-        // Four vertices per thread per step, their row lookups issued together
+        // Eight vertices per thread per step, their row lookups issued together
         // (each is a chain of dependent loads in a batch).
-        constexpr int kProU = 4;
+        constexpr int kProU = 8;
         for (long long b0 = (long long)blockIdx.x * kBlock; b0 < (recolor ? 0ll : (long long)p.n);
              b0 += kProU * stride) {
             int64_t degs[kProU];
@@ -2477,8 +2516,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) prologue_kernel(KParams p)
 }
 
 // All rounds of a colouring (after prologue_kernel on the same stream).
-template <bool ASYNC, bool BATCH>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) color_kernel(KParams p)
+// MINB: the resident blocks per SM it is compiled for (kMinBlocks, or 2 for
+// grids of at most two blocks per SM, which then get more registers per
+// thread).
+template <bool ASYNC, bool BATCH, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
 {
     extern __shared__ __align__(128) unsigned char gc_smem[];
     Shared &sh = *reinterpret_cast<Shared *>(gc_smem);
@@ -2778,6 +2820,16 @@ cudaError_t launch_wait_probe(const KParams &p, int which, unsigned long long ti
 // launchers
 // ------------------------------------------------------------------------
 
+// SMs of the current device.
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
 template <bool A, bool B>
 static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
 {
@@ -2792,8 +2844,11 @@ static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelEx(&cfg, prologue_kernel<A, B>, p);
-    if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, color_kernel<A, B>, p);
-    return e;
+    if (e != cudaSuccess) return e;
+    if constexpr (A) {
+        if (grid <= 2 * sm_count()) return cudaLaunchKernelEx(&cfg, color_kernel<A, B, 2>, p);
+    }
+    return cudaLaunchKernelEx(&cfg, color_kernel<A, B, kMinBlocks>, p);
 }
 
 cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s)
@@ -2802,10 +2857,13 @@ cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cud
     return batch ? launch_one<false, true>(p, grid, s) : launch_one<false, false>(p, grid, s);
 }
 
-static const void *color_kernel_ptr(bool async, bool batch)
+static const void *color_kernel_ptr(bool async, bool batch, bool two = false)
 {
-    return async ? (batch ? (const void *)color_kernel<true, true> : (const void *)color_kernel<true, false>)
-                 : (batch ? (const void *)color_kernel<false, true> : (const void *)color_kernel<false, false>);
+    if (two) return batch ? (const void *)color_kernel<true, true, 2> : (const void *)color_kernel<true, false, 2>;
+    return async ? (batch ? (const void *)color_kernel<true, true, kMinBlocks>
+                          : (const void *)color_kernel<true, false, kMinBlocks>)
+                 : (batch ? (const void *)color_kernel<false, true, kMinBlocks>
+                          : (const void *)color_kernel<false, false, kMinBlocks>);
 }
 
 static const void *prologue_kernel_ptr(bool async, bool batch)
@@ -2818,7 +2876,7 @@ cudaError_t prepare_color_kernels()
 {
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
-            for (const void *f : {color_kernel_ptr(a, b), prologue_kernel_ptr(a, b)}) {
+            for (const void *f : {color_kernel_ptr(a, b), color_kernel_ptr(a, b, a != 0), prologue_kernel_ptr(a, b)}) {
                 const cudaError_t e =
                     cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
                 if (e != cudaSuccess) return e;

@@ -150,6 +150,8 @@ _SIGS = {
     "gc_debug_barrier_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "gc_debug_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_int32)]),
+    "gc_measure_gather_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lock = threading.Lock()
@@ -449,6 +451,16 @@ def gc_debug_barrier_timeout(device: int = 0, timeout_ms: int = 200):
     w = ctypes.c_int32(0)
     rc = load().gc_debug_barrier_timeout(int(device), int(timeout_ms), ctypes.byref(w))
     return int(rc), int(w.value)
+
+
+def gc_measure_gather_rate(device: int = 0, array_bytes: int = 8 << 20, blocks_per_sm: int = 2,
+                           dependent: bool = False):
+    """Random 4-byte gathers per second (in 1e9) from an array of
+    `array_bytes` on the device; returns (status, rate)."""
+    r = ctypes.c_double(0.0)
+    rc = load().gc_measure_gather_rate(int(device), int(array_bytes), int(blocks_per_sm), int(bool(dependent)),
+                                       ctypes.byref(r))
+    return int(rc), float(r.value)
 
 
 def gc_host_threads() -> int:

@@ -63,6 +63,12 @@ def test_argument_errors_need_no_device(lib):
     assert lib.gc_color_batch(None, ctypes.byref(b), 0, None, None, None, None, None) == gc.GC_ERR_ARG
     h = ctypes.c_void_p()
     assert lib.gc_ctx_create(None, 0) == gc.GC_ERR_ARG
+    r = ctypes.c_double()
+    assert lib.gc_measure_gather_rate(0, 100, 2, 0, ctypes.byref(r)) == gc.GC_ERR_ARG     # array too small
+    assert lib.gc_measure_gather_rate(0, 2 << 30, 2, 0, ctypes.byref(r)) == gc.GC_ERR_ARG  # too large
+    assert lib.gc_measure_gather_rate(0, 8 << 20, 9, 0, ctypes.byref(r)) == gc.GC_ERR_ARG  # blocks per SM
+    assert lib.gc_measure_gather_rate(0, 8 << 20, 2, 2, ctypes.byref(r)) == gc.GC_ERR_ARG  # kind
+    assert lib.gc_measure_gather_rate(0, 8 << 20, 2, 0, None) == gc.GC_ERR_ARG
 
 
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):
