@@ -75,15 +75,18 @@ __device__ __forceinline__ void st_color(int32_t *p, int v)
 static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long long timeout_ns = kBarrierTimeoutNs,
                                  unsigned sleep_ns = 64)
 {
+    // Arrival is a release (the block's writes, ordered before thread 0 by
+    // the block barrier, become visible with it) and the wait an acquire;
+    // the last block resets the count before it releases the next
+    // generation, so no block arrives at the next barrier before the reset.
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         if (nblocks > 1) {
-            unsigned gen = ld_acquire_u32(&st->bar_gen);
-            unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
-            if (arrived == nblocks) {
-                atomicExch(&st->bar_count, 0u);
-                __threadfence();
+            const unsigned gen = ld_acquire_u32(&st->bar_gen);
+            unsigned arrived;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&st->bar_count) : "memory");
+            if (arrived + 1u == nblocks) {
+                asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&st->bar_count) : "memory");
                 st_release_u32(&st->bar_gen, gen + 1u);
             } else {
                 unsigned long long t0 = global_timer();
@@ -96,7 +99,6 @@ static __device__ void grid_sync(DevState *st, unsigned nblocks, unsigned long l
                     }
                 }
             }
-            __threadfence();
         }
     }
     __syncthreads();

@@ -62,13 +62,18 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
 }
 
 // Global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of
-// 16; completion is signalled on `bar` as transaction bytes.
+// 16; completion is signalled on `bar` as transaction bytes.  The copied
+// column indices are read once per pass: their L2 lines are marked first to
+// evict, so that the stream does not push the colour array out of L2.
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
 {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
+    unsigned long long policy;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -1551,9 +1556,13 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
 // Runs `op` over the hubs (block per vertex) and then the tiles (warp per
 // 32 entries) of `in`.  Vertices found defective are appended to the
 // worklists of iteration `it` when `push` is set.
+// The first hub of block b and the first tile of warp w are fixed (b and w;
+// nbl blocks take part), the rest are claimed, so a pass whose work fits
+// the grid makes no claim at all.
 template <bool ASYNC, bool BATCH>
 __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
-                         const int32_t *R, int32_t *W, bool push, long long &mb, uint32_t &phase, int window = -1)
+                         const int32_t *R, int32_t *W, bool push, long long &mb, uint32_t &phase, unsigned nbl,
+                         int window = -1)
 {
     DevState *st = p.st;
     const int lane = threadIdx.x & 31;
@@ -1568,27 +1577,30 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
     // hubs: one block per vertex
     if (in.hn > 0) {
         int *claim = &st->pass_hub[q & (kRing - 1)];
-        for (;;) {
-            if (threadIdx.x == 0) sh.claim = atomicAdd(claim, 1);
-            __syncthreads();
-            const int h = sh.claim;
-            __syncthreads();
+        for (int h = (int)blockIdx.x;;) {
             if (h >= in.hn) break;
             const int32_t v = __ldcg(in.hub + h);
             int64_t beg, end;
             int32_t nbase, g;
             row_of<BATCH>(p, v, beg, end, nbase, g);
             // a core was coloured before round 0 and never changes
-            if (p.core_deg > 0 && end - beg > p.core_deg && __ldcg(&p.gstat[g].core_on)) continue;
-            bool d = vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
-                     op == OP_TENT;  // round 0: hubs are kept for the first repair pass
-            if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
-                atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
-                const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
-                if (idx < p.hub_cap) __stcg(out_hub + idx, v);
-                else atomicOr(&st->error, GC_EW_OVERFLOW);
-                if (op != OP_TENT) note_push_graph<BATCH>(p, g, it);
+            if (!(p.core_deg > 0 && end - beg > p.core_deg && __ldcg(&p.gstat[g].core_on))) {
+                const bool d =
+                    vertex_block<ASYNC, BATCH>(p, op, v, beg, end, nbase, R, W, in.implicit, mb, sh, it) ||
+                    op == OP_TENT;  // round 0: hubs are kept for the first repair pass
+                if (push && d && threadIdx.x == 0 && (!keep || claim_push(p, v, it))) {
+                    atomicAdd(&st->wl_packed[it & (kRing - 1)], (unsigned long long)(end - beg));
+                    const int idx = atomicAdd(&st->hub_count[it & (kRing - 1)], 1);
+                    if (idx < p.hub_cap) __stcg(out_hub + idx, v);
+                    else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    if (op != OP_TENT) note_push_graph<BATCH>(p, g, it);
+                }
             }
+            if (in.hn <= (int)nbl) break;  // every hub had a block of its own
+            __syncthreads();
+            if (threadIdx.x == 0) sh.claim = (int)nbl + atomicAdd(claim, 1);
+            __syncthreads();
+            h = sh.claim;
         }
     }
 
@@ -1598,11 +1610,10 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
         return;
     }
     int *claim = &st->pass_tile[q & (kRing - 1)];
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(claim, 1);
-        t = __shfl_sync(FULL_MASK, t, 0);
-        const long long base = (long long)t * p.tile;
+    const long long nwarps = (long long)nbl * kWarps;
+    const long long ntiles = ((long long)in.n + p.tile - 1) / p.tile;
+    for (long long t = (long long)blockIdx.x * kWarps + wid;;) {
+        const long long base = t * p.tile;
         if (base >= in.n) break;
         for (int j = 0; j < p.tile && base + j < in.n; j += 32) {
             const long long idx = base + j + lane;
@@ -1614,6 +1625,10 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
             chunk_ops<ASYNC, BATCH>(p, sh, GlobalEnts{p.col_idx}, op, it, false, in.dmax, v, beg, end, nbase, g, R,
                                     W, push, mb, lane, wid);
         }
+        if (ntiles <= nwarps) break;  // every tile had a warp of its own
+        int c = 0;
+        if (lane == 0) c = atomicAdd(claim, 1);
+        t = nwarps + __shfl_sync(FULL_MASK, c, 0);
     }
 }
 
@@ -2488,11 +2503,8 @@ __device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
             // coloured concurrently unless the graph goes strictly in id order.
             if (blockIdx.x == 0) plan_ordering<BATCH>(p, sh);
             // The core of one graph (see core_sort); its first barrier also
-            // ends plan_ordering.
-            if (p.core_deg > 0 && ld_volatile(&st->hub_all_count) > 0)
-                core_stage<BATCH>(p, sh);
-            else
-                grid_sync(st, nbl);
+            // ends plan_ordering (without a core, the end of this launch does).
+            if (p.core_deg > 0 && ld_volatile(&st->hub_all_count) > 0) core_stage<BATCH>(p, sh);
             if (blockIdx.x == 0 && threadIdx.x == 0) st->window = ld_volatile(&st->n_ordered);
         }
 
@@ -2584,7 +2596,7 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
             // those (every other vertex of U^0 = V is provably clean).
             if (ASYNC && !twop && !recolor) {
                 const bool suspects = !snap;
-                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, window);
+                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, nbl, window);
                 grid_sync(st, nbl);
                 if (blockIdx.x == 0 && threadIdx.x == 0 && it < kStamps) st->stamp[it] = global_timer();
                 if (ld_volatile(&st->error)) {
@@ -2607,7 +2619,7 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
                     // the prologue), barrier, phase 2 detection, barrier.
                     if (ASYNC || it > 1) {
                         run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false,
-                                               mb, phase, window);
+                                               mb, phase, nbl, window);
                         grid_sync(st, nbl);
                         if (ld_volatile(&st->error)) {
                             alive = false;
@@ -2615,10 +2627,10 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
                         }
                     }
                     run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb,
-                                           phase);
+                                           phase, nbl);
                 } else {
                     // Algorithm 3: fused detect-and-recolour over U.
-                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb, phase);
+                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb, phase, nbl);
                     last_written = W;
                 }
                 grid_sync(st, nbl);
