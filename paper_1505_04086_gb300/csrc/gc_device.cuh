@@ -121,40 +121,86 @@ __device__ __forceinline__ bool on_tie_side(int tie, int32_t u, int32_t v)
 // next call (it must be zero on entry).
 static __device__ void colour_stats(const int32_t *c, int32_t n, DevState *st, uint32_t *bitmap)
 {
+    constexpr int kSmemWords = 32;  // colours below 1024 are collected per block first
     __shared__ int acc;
     __shared__ bool last;
+    __shared__ int smax;
+    __shared__ uint32_t sbm[kSmemWords];
+    if (threadIdx.x < kSmemWords) sbm[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
     int mx = 0;
     unsigned long long low = 0;  // colours 0..63, OR-reduced per warp
+    bool wrote = false;          // this thread updated the global bitmap
     auto note = [&](int x) {
         mx = max(mx, x);
-        if (x >= 0 && x < 64) low |= 1ull << x;
-        else if (x >= 64 && x < kStatBitmapWords * 32) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+        if (x >= 0 && x < 64) {
+            low |= 1ull << x;
+        } else if (x >= 64 && x < kSmemWords * 32) {
+            atomicOr(&sbm[x >> 5], 1u << (x & 31));
+        } else if (x >= kSmemWords * 32 && x < kStatBitmapWords * 32) {
+            atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+            wrote = true;
+        }
     };
-    // eight independent loads in flight per thread, then the remainder
+    // eight independent loads in flight per thread (16-byte vectors when the
+    // array is 16-byte aligned), then the remainder
     constexpr int kU = 8;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (; i + (kU - 1) * stride < n; i += kU * stride) {
-        int x[kU];
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long i = tid;
+    if ((reinterpret_cast<uintptr_t>(c) & 15u) == 0) {
+        const int4 *c4 = reinterpret_cast<const int4 *>(c);
+        const long long n4 = n / 4;
+        for (; i + (kU - 1) * stride < n4; i += kU * stride) {
+            int4 x[kU];
 #pragma unroll
-        for (int q = 0; q < kU; ++q) x[q] = __ldcg(c + i + q * stride);
+            for (int q = 0; q < kU; ++q) x[q] = __ldcg(c4 + i + q * stride);
 #pragma unroll
-        for (int q = 0; q < kU; ++q) note(x[q]);
+            for (int q = 0; q < kU; ++q) {
+                note(x[q].x);
+                note(x[q].y);
+                note(x[q].z);
+                note(x[q].w);
+            }
+        }
+        for (; i < n4; i += stride) {
+            const int4 x = __ldcg(c4 + i);
+            note(x.x);
+            note(x.y);
+            note(x.z);
+            note(x.w);
+        }
+        if (n4 * 4 + tid < n) note(__ldcg(c + n4 * 4 + tid));  // the last n % 4
+    } else {
+        for (; i + (kU - 1) * stride < n; i += kU * stride) {
+            int x[kU];
+#pragma unroll
+            for (int q = 0; q < kU; ++q) x[q] = __ldcg(c + i + q * stride);
+#pragma unroll
+            for (int q = 0; q < kU; ++q) note(x[q]);
+        }
+        for (; i < n; i += stride) note(__ldcg(c + i));
     }
-    for (; i < n; i += stride) note(__ldcg(c + i));
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_down_sync(FULL_MASK, mx, o));
         low |= __shfl_down_sync(FULL_MASK, low, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (mx) atomicMax(&st->max_color, mx);
-        if (low & 0xffffffffull) atomicOr(&bitmap[0], (uint32_t)low);
-        if (low >> 32) atomicOr(&bitmap[1], (uint32_t)(low >> 32));
+        if (mx) atomicMax(&smax, mx);
+        if (low & 0xffffffffull) atomicOr(&sbm[0], (uint32_t)low);
+        if (low >> 32) atomicOr(&sbm[1], (uint32_t)(low >> 32));
     }
-    __threadfence();  // this thread's updates land before the block reports done
+    __syncthreads();
+    // one warp publishes the block's words and maximum; every thread's own
+    // global updates (colours >= 1024) land before the block reports done
+    if (threadIdx.x < kSmemWords) {
+        if (sbm[threadIdx.x]) atomicOr(&bitmap[threadIdx.x], sbm[threadIdx.x]);
+        if (threadIdx.x == 0 && smax) atomicMax(&st->max_color, smax);
+    }
+    if (wrote || threadIdx.x < kSmemWords) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         last = atomicAdd(&st->stats_done, 1u) == gridDim.x - 1;
         acc = 0;
     }
