@@ -101,6 +101,10 @@ int grid_for(gc_ctx *c, bool async, bool batch, bool dist2, const Resolved &r, i
     return (int)grid;
 }
 
+// The device state, then (single graphs) the graph's statistics.
+constexpr size_t kStateHead = (sizeof(DevState) + 255) / 256 * 256;
+constexpr size_t kStateBytes = kStateHead + sizeof(gc::GraphStat);
+
 // Event record on s; while a CUDA graph is being captured the record
 // becomes a node of the graph, so timing and completion work on replays.
 cudaError_t record(gc_ctx *c, cudaEvent_t ev, cudaStream_t s)
@@ -136,7 +140,10 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.r0mask = masks ? c->r0mask.as<uint64_t>() : nullptr;
     p.core_deg = gc::core_applies(mode, p.touched != nullptr) ? r.core_deg : 0;
     p.done = c->done.as<int32_t>();
-    p.gstat = c->gstat.as<gc::GraphStat>();
+    // one graph: its statistics sit right after the state, so that one
+    // memset clears both
+    p.gstat = p.G <= 1 ? reinterpret_cast<gc::GraphStat *>(c->st.as<char>() + kStateHead)
+                       : c->gstat.as<gc::GraphStat>();
     p.uofs = c->uofs.as<int64_t>();
     p.olist = c->olist.as<int32_t>();
     p.pitems = c->pitems.as<int64_t>();
@@ -151,9 +158,13 @@ int enqueue(gc_ctx *c, KParams &p, bool batch, uint32_t mode, const Resolved &r,
     p.mid_all = c->mid_all.as<int32_t>();
     p.hub_cap = (int32_t)n;
 
-    if ((e = cudaMemsetAsync(c->st.p, 0, sizeof(DevState), s)) != cudaSuccess) return cuda_status(e);
-    if ((e = cudaMemsetAsync(c->gstat.p, 0, (size_t)std::max(p.G, 1) * sizeof(gc::GraphStat), s)) != cudaSuccess)
-        return cuda_status(e);
+    if (p.G <= 1) {
+        if ((e = cudaMemsetAsync(c->st.p, 0, kStateBytes, s)) != cudaSuccess) return cuda_status(e);
+    } else {
+        if ((e = cudaMemsetAsync(c->st.p, 0, sizeof(DevState), s)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemsetAsync(c->gstat.p, 0, (size_t)p.G * sizeof(gc::GraphStat), s)) != cudaSuccess)
+            return cuda_status(e);
+    }
     const bool stats = !(mode & GC_NO_COLOR_STATS);
     p.stats_bitmap = stats ? c->bitmap.as<uint32_t>() : nullptr;  // computed at the end of the colouring kernel
     if (batch && (e = gc::launch_build_lut(p.vtx_off, p.G, p.n, c->lut.as<int32_t>(), s)) != cudaSuccess)
@@ -334,7 +345,7 @@ int gc_ctx_create(gc_ctx **out, int device)
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&c->rs_host, kRoundSizesDev * sizeof(int32_t));
     if (e != cudaSuccess) rc = cuda_status(e);
-    if (rc == GC_OK && (!c->st.reserve(sizeof(DevState)) ||
+    if (rc == GC_OK && (!c->st.reserve(kStateBytes) ||
                         !c->bitmap.reserve(gc::kStatBitmapWords * sizeof(uint32_t)) ||
                         !c->round_sizes.reserve(kRoundSizesDev * sizeof(int32_t))))
         rc = GC_ERR_OOM;
