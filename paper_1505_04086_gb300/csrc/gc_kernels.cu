@@ -311,7 +311,7 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
     const int cv = ld_color<ASYNC>(R + v);
     mb += 4;
     bool d;
-    if (ASYNC && op == OP_RSOC && it == 1 && p.r0mask && !implicit) {
+    if (ASYNC && !BATCH && op == OP_RSOC && it == 1 && p.r0mask && !implicit) {  // (masks: one graph only)
         // First repair after round 0: only the neighbours this vertex read
         // as uncoloured there can share its colour (see chunk_tent_ordered).
         unsigned long long m = __ldcg(reinterpret_cast<const unsigned long long *>(p.r0mask) + v);
@@ -319,10 +319,26 @@ __device__ __forceinline__ bool vertex_thread(const KParams &p, const E &ent, in
         bool def = cv == 0;
         t = 0;
         while (m) {
-            const int i = __ffsll((long long)m) - 1;
-            m &= m - 1;
-            ++t;
-            def |= ld_color<ASYNC>(R + nbase + row[i]) == cv;
+            // four named positions at a time: their entries, then their
+            // colours, loaded together
+            constexpr int kQ = 4;
+            int pos[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                pos[q] = m ? __ffsll((long long)m) - 1 : -1;
+                m &= m - 1;
+            }
+            int32_t u[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) u[q] = pos[q] >= 0 ? nbase + row[pos[q]] : 0;
+            int c[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) c[q] = pos[q] >= 0 ? ld_color<ASYNC>(R + u[q]) : -1;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                t += pos[q] >= 0;
+                def |= c[q] == cv;
+            }
         }
         d = def;
         mb += 8;  // the mask
@@ -768,19 +784,23 @@ __device__ __forceinline__ int resolve_in_order(unsigned long long ext, unsigned
 // order from v0; ids in [max(v0, cbase - kRingIds), cbase) were coloured by
 // this warp and their colours sit in `ring`; with skip_higher no id above
 // the chunk is coloured yet (the graph has no vertex coloured elsewhere).
-template <class E, bool RING>
+// LEAN: the caller has checked that every vertex of the chunk takes the
+// thread path (no hub, no warp-path lane), that lower ids keep their colours
+// and that GC_FF_KEEPERS is off; the checks for those cases drop out of the
+// per-entry work.
+template <class E, bool RING, bool LEAN = false>
 __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cbase, int32_t v, int64_t beg,
                                    int64_t end, int32_t nbase, int32_t *C, long long &mb, uint32_t *bm, int lane,
                                    int dmax, uint16_t *ring = nullptr, long long v0 = 0, bool skip_higher = false,
                                    int32_t unclaimed = INT32_MAX)
 {
     const int deg = (int)(end - beg);
-    const int tie = p.tie;
-    const bool hub = v >= 0 && deg > dmax;  // coloured before this pass
-    const bool mid = v >= 0 && !hub && deg > p.t1;
+    const int tie = LEAN ? (int)TIE_LOWER : p.tie;
+    const bool hub = !LEAN && v >= 0 && deg > dmax;  // coloured before this pass
+    const bool mid = !LEAN && v >= 0 && !hub && deg > p.t1;
     const bool thr = v >= 0 && !hub && !mid;
-    const unsigned hubmask = __ballot_sync(FULL_MASK, hub);
-    const unsigned midmask = __ballot_sync(FULL_MASK, mid);
+    const unsigned hubmask = LEAN ? 0u : __ballot_sync(FULL_MASK, hub);
+    const unsigned midmask = LEAN ? 0u : __ballot_sync(FULL_MASK, mid);
     unsigned long long ext = 0;
     unsigned low = 0;
     const int32_t cb32 = (int32_t)cbase;  // ids are below 2^31
@@ -801,7 +821,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     // up to v.
     // With degree tiers the higher neighbours read here may be final
     // colours of an earlier tier, which no later round inspects: read them.
-    const bool keepers = (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
+    const bool keepers = !LEAN && (p.mode & GC_FF_KEEPERS) != 0 && !(p.mode & GC_TIERS);
     // An ordered graph whose higher ids are all uncoloured (skip_higher)
     // gains nothing from the part of a row above v either.
     const bool keep = keepers || (RING && skip_higher);
@@ -1527,7 +1547,15 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
         bool sus = false;
         if (staged) {
             const StagedEnts ent{sh.seg[wid][slot], soff};
-            if (ordered)
+            // one graph, every lane on the thread path, lower ids keep, no
+            // keepers
+            const bool lean = !BATCH && ordered && p.tie == TIE_LOWER && !(p.mode & GC_FF_KEEPERS) &&
+                              !__any_sync(FULL_MASK, v >= 0 && (cur.deg > in.dmax || cur.deg > p.t1));
+            if (lean)
+                sus = chunk_tent_ordered<StagedEnts, false, !BATCH>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
+                                                                    sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
+                                                                    unclaimed);
+            else if (ordered)
                 sus = chunk_tent_ordered<StagedEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
                                                             sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
                                                             unclaimed);
