@@ -1496,6 +1496,13 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
                                 !(p.mode & (GC_TIERS | GC_FF_KEEPERS)) && window <= 0 &&
                                 __ldcg(&p.gstat[0].hubs) == 0u;
 
+    // One graph with no hub and no vertex of degree above kT1Max, lower ids
+    // keep, no keepers: its round-0 chunks take the lean colouring whenever
+    // all their lanes are on the thread path.  (Graphs with wider rows keep
+    // the one general form: alternating between the two made R-MAT's round
+    // 0 slower.)
+    const bool lean_graph = !BATCH && ordered && p.tie == TIE_LOWER && !(p.mode & GC_FF_KEEPERS) &&
+                            __ldcg(&p.gstat[0].hubs) == 0u && __ldcg(&p.gstat[0].wide) == 0u;
     int t = 0;
     if (lane == 0) t = atomicAdd(claim, 1);
     t = __shfl_sync(FULL_MASK, t, 0);
@@ -1547,10 +1554,9 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
         bool sus = false;
         if (staged) {
             const StagedEnts ent{sh.seg[wid][slot], soff};
-            // one graph, every lane on the thread path, lower ids keep, no
-            // keepers
-            const bool lean = !BATCH && ordered && p.tie == TIE_LOWER && !(p.mode & GC_FF_KEEPERS) &&
-                              !__any_sync(FULL_MASK, v >= 0 && (cur.deg > in.dmax || cur.deg > p.t1));
+            // every lane on the thread path (checked per chunk in a graph
+            // of uniform low degree)
+            const bool lean = lean_graph && !__any_sync(FULL_MASK, v >= 0 && (cur.deg > in.dmax || cur.deg > p.t1));
             if (lean)
                 sus = chunk_tent_ordered<StagedEnts, false, !BATCH>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
                                                                     sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
