@@ -788,12 +788,22 @@ __device__ __forceinline__ int resolve_in_order(unsigned long long ext, unsigned
 // thread path (no hub, no warp-path lane), that lower ids keep their colours
 // and that GC_FF_KEEPERS is off; the checks for those cases drop out of the
 // per-entry work.
+// What a lean chunk's lane read as uncoloured on its tie side: the first
+// two such neighbours (u0, u1), how many there were (zc) and the colour the
+// lane took (cv), so that the suspect can be checked again a chunk later.
+struct SusHint {
+    int32_t u0, u1;
+    int zc;
+    int cv;
+};
+
 template <class E, bool RING, bool LEAN = false>
 __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cbase, int32_t v, int64_t beg,
                                    int64_t end, int32_t nbase, int32_t *C, long long &mb, uint32_t *bm, int lane,
                                    int dmax, uint16_t *ring = nullptr, long long v0 = 0, bool skip_higher = false,
-                                   int32_t unclaimed = INT32_MAX)
+                                   int32_t unclaimed = INT32_MAX, SusHint *hint = nullptr)
 {
+    if (LEAN && hint) hint->zc = 0;
     const int deg = (int)(end - beg);
     const int tie = LEAN ? (int)TIE_LOWER : p.tie;
     const bool hub = !LEAN && v >= 0 && deg > dmax;  // coloured before this pass
@@ -881,6 +891,11 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
                 if (outside[q] && c[q] == 0 && on_tie_side(tie, u[q], v)) {
                     suspect = true;
                     zmask |= 1ull << (i + q);  // i + q < deg <= t1 <= 62
+                    if (LEAN && hint) {
+                        if (hint->zc == 0) hint->u0 = u[q];
+                        else if (hint->zc == 1) hint->u1 = u[q];
+                        ++hint->zc;
+                    }
                 }
             }
             if (keep && u[kUnroll - 1] < 0) break;  // row ended, or passed v
@@ -888,6 +903,7 @@ __device__ bool chunk_tent_ordered(const KParams &p, const E &ent, long long cba
     }
     __syncwarp();
     const int mine = resolve_in_order(ext, low, thr, lane);
+    if (LEAN && hint) hint->cv = mine;
     if (thr) {
         st_color<true>(C + v, mine);
         mb += 8 + 8ll * nread - 4ll * nskip + 4;  // index only for the unread colours
@@ -1443,7 +1459,7 @@ __device__ __forceinline__ void chunk_of(const KParams &p, long long vc, bool vi
 // tiles it claims in id order, staging chunk j+1 while it works on chunk j.
 // The asynchronous tentative pass resolves lanes in id order and keeps at
 // most `window` tiles in flight (window <= 0: no limit).
-template <bool ASYNC, bool BATCH>
+template <bool ASYNC, bool BATCH, bool WIDE>
 __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
                                 const int32_t *R, int32_t *W, bool push, long long &mb, int window,
                                 uint32_t &phase)
@@ -1500,8 +1516,10 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
     // keep, no keepers: its round-0 chunks take the lean colouring whenever
     // all their lanes are on the thread path.  (Graphs with wider rows keep
     // the one general form: alternating between the two made R-MAT's round
-    // 0 slower.)
-    const bool lean_graph = !BATCH && ordered && p.tie == TIE_LOWER && !(p.mode & GC_FF_KEEPERS) &&
+    // 0 slower.)  Only in the build for at most two blocks per SM (WIDE: 128
+    // registers); in the three-block build, at 80 registers, the extra code
+    // made every graph's round 0 slower through more spilling.
+    const bool lean_graph = WIDE && !BATCH && ordered && p.tie == TIE_LOWER && !(p.mode & GC_FF_KEEPERS) &&
                             __ldcg(&p.gstat[0].hubs) == 0u && __ldcg(&p.gstat[0].wide) == 0u;
     int t = 0;
     if (lane == 0) t = atomicAdd(claim, 1);
@@ -1509,6 +1527,27 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
     LaneRow cur, nxt;
     SusBuf sbuf;
     int slot = 0;
+    // The suspects of a lean chunk wait one chunk: by then the tie-side
+    // neighbours each read as uncoloured (at most two are kept) have almost
+    // always been coloured, and a round-0 colour is final for the round, so
+    // a suspect whose such neighbours all hold colours other than its own
+    // has no clash on its tie side and is dropped from the first repair.
+    bool pend = false;  // warp-uniform: the previous chunk's suspects wait
+    bool psus = false;
+    int32_t pv = -1;
+    int pdeg = 0;
+    SusHint ph{0, 0, 0, 0};
+    auto push_pending = [&]() {
+        bool still = psus;
+        if (psus && ph.zc <= 2) {
+            const int c0 = ld_color<true>(W + ph.u0);
+            const int c1 = ph.zc == 2 ? ld_color<true>(W + ph.u1) : -1;
+            mb += 4ll * ph.zc;
+            still = c0 == 0 || c0 == ph.cv || (ph.zc == 2 && (c1 == 0 || c1 == ph.cv));
+        }
+        sus_push(p, sh, sbuf, still, pv, pdeg, it, lane, wid);
+        pend = false;
+    };
     {
         long long cb = -1, cend = 0;
         if (t < ntiles) chunk_of<BATCH>(p, (long long)t * cpt, ordered, n, cb, cend);
@@ -1517,7 +1556,10 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
     for (;;) {
         const long long cb = sh.slot[wid][slot].cb;
         if (cb < 0) {
-            if (ordered && push) sus_flush(p, sh, sbuf, it, lane, wid);
+            if (ordered && push) {
+                if (pend) push_pending();
+                sus_flush(p, sh, sbuf, it, lane, wid);
+            }
             break;
         }
         const long long soff = sh.slot[wid][slot].soff;
@@ -1552,15 +1594,17 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
             if (first_free < n) unclaimed = (int32_t)first_free;
         }
         bool sus = false;
+        bool lean = false;
+        SusHint hint{0, 0, 0, 0};
         if (staged) {
             const StagedEnts ent{sh.seg[wid][slot], soff};
             // every lane on the thread path (checked per chunk in a graph
             // of uniform low degree)
-            const bool lean = lean_graph && !__any_sync(FULL_MASK, v >= 0 && (cur.deg > in.dmax || cur.deg > p.t1));
+            lean = lean_graph && !__any_sync(FULL_MASK, v >= 0 && (cur.deg > in.dmax || cur.deg > p.t1));
             if (lean)
-                sus = chunk_tent_ordered<StagedEnts, false, !BATCH>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
+                sus = chunk_tent_ordered<StagedEnts, false, WIDE && !BATCH>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
                                                                     sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
-                                                                    unclaimed);
+                                                                    unclaimed, &hint);
             else if (ordered)
                 sus = chunk_tent_ordered<StagedEnts, false>(p, ent, cb, v, cur.beg, end, cur.nbase, W, mb,
                                                             sh.warp_bm[wid], lane, in.dmax, nullptr, 0, false,
@@ -1579,7 +1623,18 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
                                         push, mb, lane, wid);
         }
         // Round 0 with push: the suspects form the first repair worklist.
-        if (ordered && push) sus_push(p, sh, sbuf, sus, v, cur.deg, it, lane, wid);
+        if (ordered && push) {
+            if (pend) push_pending();
+            if (WIDE && lean && p.r0mask) {
+                pend = true;
+                psus = sus;
+                pv = v;
+                pdeg = cur.deg;
+                ph = hint;
+            } else {
+                sus_push(p, sh, sbuf, sus, v, cur.deg, it, lane, wid);
+            }
+        }
         if (ordered && window > 0 && last_of_tile) publish_tile_done(p, tile, lane);
         __syncwarp();  // every lane is done with seg[slot] before it is refilled
         cur = nxt;
@@ -1593,7 +1648,7 @@ __device__ __forceinline__ void implicit_staged(const KParams &p, Shared &sh, in
 // The first hub of block b and the first tile of warp w are fixed (b and w;
 // nbl blocks take part), the rest are claimed, so a pass whose work fits
 // the grid makes no claim at all.
-template <bool ASYNC, bool BATCH>
+template <bool ASYNC, bool BATCH, bool WIDE>
 __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, const PassIn &in,
                          const int32_t *R, int32_t *W, bool push, long long &mb, uint32_t &phase, unsigned nbl,
                          int window = -1)
@@ -1640,7 +1695,7 @@ __device__ void run_pass(const KParams &p, Shared &sh, int op, int q, int it, co
 
     // tiles: one warp per group of `tile` consecutive worklist entries
     if (in.implicit) {
-        implicit_staged<ASYNC, BATCH>(p, sh, op, q, it, in, R, W, push, mb, window, phase);
+        implicit_staged<ASYNC, BATCH, WIDE>(p, sh, op, q, it, in, R, W, push, mb, window, phase);
         return;
     }
     int *claim = &st->pass_tile[q & (kRing - 1)];
@@ -2630,7 +2685,7 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
             // those (every other vertex of U^0 = V is provably clean).
             if (ASYNC && !twop && !recolor) {
                 const bool suspects = !snap;
-                run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, nbl, window);
+                run_pass<ASYNC, BATCH, (MINB <= 2)>(p, sh, OP_TENT, q++, it, in, R, R, suspects, mb, phase, nbl, window);
                 grid_sync(st, nbl);
                 if (blockIdx.x == 0 && threadIdx.x == 0 && it < kStamps) st->stamp[it] = global_timer();
                 if (ld_volatile(&st->error)) {
@@ -2652,7 +2707,7 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
                     // deterministic mode iteration 1's phase 1 is the fill of
                     // the prologue), barrier, phase 2 detection, barrier.
                     if (ASYNC || it > 1) {
-                        run_pass<ASYNC, BATCH>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false,
+                        run_pass<ASYNC, BATCH, (MINB <= 2)>(p, sh, OP_TENT, q++, it, in, p.cA, ASYNC ? p.cA : p.cB, false,
                                                mb, phase, nbl, window);
                         grid_sync(st, nbl);
                         if (ld_volatile(&st->error)) {
@@ -2660,11 +2715,11 @@ __global__ void __launch_bounds__(kBlock, MINB) color_kernel(KParams p)
                             break;
                         }
                     }
-                    run_pass<ASYNC, BATCH>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb,
+                    run_pass<ASYNC, BATCH, (MINB <= 2)>(p, sh, OP_DETECT, q++, it, in, ASYNC ? p.cA : p.cB, p.cA, true, mb,
                                            phase, nbl);
                 } else {
                     // Algorithm 3: fused detect-and-recolour over U.
-                    run_pass<ASYNC, BATCH>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb, phase, nbl);
+                    run_pass<ASYNC, BATCH, (MINB <= 2)>(p, sh, OP_RSOC, q++, it, in, R, W, true, mb, phase, nbl);
                     last_written = W;
                 }
                 grid_sync(st, nbl);
