@@ -175,6 +175,8 @@ struct KParams {
                                // tie-side neighbours read as uncoloured (null: not kept)
     int32_t core_deg;          // asynchronous: each graph's vertices of degree > core_deg (and > t2) are
                                // coloured first, one at a time in decreasing degree (0: no core)
+    int32_t round_blocks;      // blocks of the rounds kernel (set by the launcher; the prologue may run on
+                               // more, and plans round 0 for these)
 };
 
 // Batched colouring with per-graph row-pointer offsets (the server's waves:

@@ -1754,7 +1754,8 @@ __device__ __noinline__ void plan_ordering(const KParams &p, Shared &sh)
     const int window = p.window;
     const bool tiers = (p.mode & GC_TIERS) != 0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const long long warps = (long long)gridDim.x * kWarps;
+    // the warps of the rounds kernel, which run the plan
+    const long long warps = (long long)(p.round_blocks > 0 ? p.round_blocks : (int)gridDim.x) * kWarps;
     const long long budget = min(warps, (long long)p.pitems_cap) * 7 / 8;
     auto graph_n = [&](int g) -> long long {
         return BATCH ? __ldg(p.vtx_off + g + 1) - __ldg(p.vtx_off + g) : (long long)p.n;
@@ -2944,12 +2945,29 @@ static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, prologue_kernel<A, B>, p);
+    // The prologue (a streaming pass over V, the core's bit matrices) runs
+    // on as many resident blocks as it can hold when the rounds kernel has
+    // at least two per SM; it plans round 0 for the rounds kernel's grid.
+    static int prologue_occ = 0;  // resident prologue blocks per SM (the same on every device of this build)
+    const int sms = sm_count();
+    if (prologue_occ == 0) {
+        int a = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, prologue_kernel<A, B>, kBlock, sizeof(Shared)) ==
+            cudaSuccess)
+            prologue_occ = a;
+        else
+            cudaGetLastError();
+    }
+    KParams q = p;
+    q.round_blocks = grid;
+    cudaLaunchConfig_t pcfg = cfg;
+    if (sms > 0 && grid >= 2 * sms && prologue_occ * sms > grid) pcfg.gridDim = dim3((unsigned)(prologue_occ * sms));
+    cudaError_t e = cudaLaunchKernelEx(&pcfg, prologue_kernel<A, B>, q);
     if (e != cudaSuccess) return e;
     if constexpr (A) {
-        if (grid <= 2 * sm_count()) return cudaLaunchKernelEx(&cfg, color_kernel<A, B, 2>, p);
+        if (grid <= 2 * sms) return cudaLaunchKernelEx(&cfg, color_kernel<A, B, 2>, q);
     }
-    return cudaLaunchKernelEx(&cfg, color_kernel<A, B, kMinBlocks>, p);
+    return cudaLaunchKernelEx(&cfg, color_kernel<A, B, kMinBlocks>, q);
 }
 
 cudaError_t launch_color(const KParams &p, bool async, bool batch, int grid, cudaStream_t s)
