@@ -268,7 +268,8 @@ void gc_ctx_destroy(gc_ctx *ctx);
  * host or device memory (host arrays are staged through the device).
  * Uses a per-host-thread default context on the current device.
  * colors_out: n int32 entries, written on success and on
- * GC_ERR_NO_CONVERGENCE (the colouring at the cap).
+ * GC_ERR_NO_CONVERGENCE (the colouring at the cap); after any other error
+ * raised by the colouring its contents are unspecified.
  * stats_out may be NULL.
  */
 int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode,

@@ -553,17 +553,20 @@ int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t *
     gc_csr d = *csr;
     cudaStream_t s = nullptr;
     cudaError_t e;
+    // Uploads, colouring and the download of the colours are enqueued on
+    // one stream and waited for once (from pinned host memory the copies
+    // run without blocking the host).
     if (!rp_dev) {
         if (!c->stage_rp.reserve(((size_t)n + 1) * sizeof(int32_t))) return GC_ERR_OOM;
-        if ((e = cudaMemcpy(c->stage_rp.p, csr->row_ptr, ((size_t)n + 1) * sizeof(int32_t),
-                            cudaMemcpyHostToDevice)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(c->stage_rp.p, csr->row_ptr, ((size_t)n + 1) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return cuda_status(e);
         d.row_ptr = c->stage_rp.as<int32_t>();
     }
     if (!ci_dev) {
         if (!c->stage_ci.reserve((size_t)nnz * sizeof(int32_t))) return GC_ERR_OOM;
-        if ((e = cudaMemcpy(c->stage_ci.p, csr->col_idx, (size_t)nnz * sizeof(int32_t), cudaMemcpyHostToDevice)) !=
-            cudaSuccess)
+        if ((e = cudaMemcpyAsync(c->stage_ci.p, csr->col_idx, (size_t)nnz * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 s)) != cudaSuccess)
             return cuda_status(e);
         d.col_idx = c->stage_ci.as<int32_t>();
     }
@@ -573,12 +576,17 @@ int gc_color(const gc_csr *csr, int32_t n, int64_t nnz, uint32_t mode, int32_t *
         out = c->stage_col.as<int32_t>();
     }
     int rc = gc_color_async(c, &d, n, nnz, mode, nullptr, out, s);
-    if (rc != GC_OK) return rc;
-    rc = gc_ctx_stats(c, stats_out);
-    if (!out_dev && (rc == GC_OK || rc == GC_ERR_NO_CONVERGENCE || rc == GC_ERR_CHECK)) {
-        if ((e = cudaMemcpy(colors_out, out, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return cuda_status(e);
+    if (rc != GC_OK) {
+        cudaStreamSynchronize(s);  // the uploads read the caller's arrays
+        return rc;
     }
+    if (!out_dev && (e = cudaMemcpyAsync(colors_out, out, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) !=
+                        cudaSuccess) {
+        cudaStreamSynchronize(s);
+        return cuda_status(e);
+    }
+    rc = gc_ctx_stats(c, stats_out);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess && rc == GC_OK) rc = cuda_status(e);
     return rc;
 }
 
