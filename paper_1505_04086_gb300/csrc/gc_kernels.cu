@@ -2407,10 +2407,98 @@ __device__ __forceinline__ void prologue(const KParams &p, Shared &sh)
                 if (keep) p.mark[v] = 0;
             }
         }
+        // One graph, asynchronous, 16-byte aligned row pointers and colours:
+        // groups of four consecutive vertices, their row pointers read as one
+        // 16-byte load (plus the next group's first), four groups per thread
+        // per step (16 vertices: one step covers a 2^21-vertex graph), the
+        // colours cleared with 16-byte stores.
+        const bool vec = !BATCH && ASYNC && !recolor && !keep &&
+                         (reinterpret_cast<uintptr_t>(p.row_ptr) & 15u) == 0 &&
+                         (reinterpret_cast<uintptr_t>(p.cA) & 15u) == 0;
+        if (vec) {
+            auto append = [&](bool hub, bool midv, int32_t v) {  // every lane of the warp calls it
+                const unsigned m = __ballot_sync(FULL_MASK, hub);
+                if (m) {
+                    const int leader = __ffs(m) - 1;
+                    int ob = 0;
+                    if (lane == leader) ob = atomicAdd(&st->hub_all_count, __popc(m));
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (hub) {
+                        const int o = ob + __popc(m & ((1u << lane) - 1u));
+                        if (o < p.hub_cap) __stcg(p.hub_all + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    }
+                }
+                const unsigned mm = __ballot_sync(FULL_MASK, midv);
+                if (mm) {
+                    const int leader = __ffs(mm) - 1;
+                    int ob = 0;
+                    if (lane == leader) ob = atomicAdd(&st->mid_all_count, __popc(mm));
+                    ob = __shfl_sync(FULL_MASK, ob, leader);
+                    if (midv) {
+                        const int o = ob + __popc(mm & ((1u << lane) - 1u));
+                        if (o < p.n) __stcg(p.mid_all + o, v);
+                        else atomicOr(&st->error, GC_EW_OVERFLOW);
+                    }
+                }
+            };
+            auto classify = [&](bool valid, int32_t v, int64_t deg) {
+                bool hub = false, midv = false;
+                if (valid) {
+                    hub = deg > p.t2;
+                    midv = tiers && !hub && deg > p.t1;
+                    if (hub) atomicAdd(&p.gstat[0].hubs, 1u);
+                    if (!hub && deg > kT1Max && __ldcg(&p.gstat[0].wide) == 0u) atomicOr(&p.gstat[0].wide, 1u);
+                }
+                append(hub, midv, v);
+            };
+            constexpr int kG = 4;
+            const long long n4 = (long long)p.n / 4;
+            const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+            const int4 *rp4 = reinterpret_cast<const int4 *>(p.row_ptr);
+            int4 *c4 = reinterpret_cast<int4 *>(p.cA);
+            for (long long base = 0; base < n4; base += kG * stride) {
+                int4 r[kG];
+                int32_t nx[kG];
+#pragma unroll
+                for (int q = 0; q < kG; ++q) {
+                    const long long gi = base + q * stride + tid;
+                    r[q] = make_int4(0, 0, 0, 0);
+                    nx[q] = 0;
+                    if (gi < n4) {
+                        r[q] = __ldg(rp4 + gi);
+                        nx[q] = __ldg(p.row_ptr + 4 * gi + 4);  // <= row_ptr[n]
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kG; ++q) {
+                    const long long gi = base + q * stride + tid;
+                    const bool ok = gi < n4;
+                    const int32_t v = (int32_t)(4 * gi);
+                    classify(ok, v, (int64_t)r[q].y - r[q].x);
+                    classify(ok, v + 1, (int64_t)r[q].z - r[q].y);
+                    classify(ok, v + 2, (int64_t)r[q].w - r[q].z);
+                    classify(ok, v + 3, (int64_t)nx[q] - r[q].w);
+                    if (ok) __stcg(c4 + gi, make_int4(0, 0, 0, 0));
+                }
+            }
+            // the last n % 4 vertices, one per thread (every lane of a warp
+            // takes part in the appends)
+            {
+                const long long vi = 4 * n4 + tid;
+                const bool ok = vi < p.n;
+                int64_t deg = 0;
+                if (ok) {
+                    deg = (int64_t)__ldg(p.row_ptr + vi + 1) - __ldg(p.row_ptr + vi);
+                    st_color<false>(p.cA + vi, 0);
+                }
+                if (tid < 32) classify(ok, (int32_t)vi, deg);  // n % 4 < 32: block 0, warp 0
+            }
+        }
         // Eight vertices per thread per step, their row lookups issued together
         // (each is a chain of dependent loads in a batch).
         constexpr int kProU = 8;
-        for (long long b0 = (long long)blockIdx.x * kBlock; b0 < (recolor ? 0ll : (long long)p.n);
+        for (long long b0 = (long long)blockIdx.x * kBlock; b0 < ((recolor || vec) ? 0ll : (long long)p.n);
              b0 += kProU * stride) {
             int64_t degs[kProU];
             int32_t gs[kProU];
