@@ -3036,7 +3036,7 @@ static cudaError_t launch_one(const KParams &p, int grid, cudaStream_t s)
     // The prologue (a streaming pass over V, the core's bit matrices) runs
     // on as many resident blocks as it can hold when the rounds kernel has
     // at least two per SM; it plans round 0 for the rounds kernel's grid.
-    static int prologue_occ = 0;  // resident prologue blocks per SM (the same on every device of this build)
+    static int prologue_occ = 0;  // resident prologue blocks per SM (the same on every sm_103a device)
     const int sms = sm_count();
     if (prologue_occ == 0) {
         int a = 0;

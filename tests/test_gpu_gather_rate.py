@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 def test_gather_rate_is_plausible(dependent):
     rc, rate = gc.gc_measure_gather_rate(0, 8 << 20, 2, dependent)
     assert rc == gc.GC_OK, gc.gc_strerror(rc)
-    # an L2-resident array: between 10 and 5000 G loads/s on any GPU this builds for
+    # an L2-resident array: between 10 and 5000 G loads/s on any sm_103a GPU
     assert 10.0 < rate < 5000.0, rate
 
 
